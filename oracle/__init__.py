@@ -1,0 +1,269 @@
+"""FP64 CPU oracle of the multi-field VoF step (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product path never imports it.
+The C source (``oracle.c``) shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (no FMA contraction, so every machine
+    rounds the same way)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            L.oracle_plic_volume.restype = C.c_double
+            L.oracle_plic_volume.argtypes = [_dp, C.c_double]
+            L.oracle_plic_alpha.restype = C.c_double
+            L.oracle_plic_alpha.argtypes = [_dp, C.c_double]
+            for f in ("oracle_youngs", "oracle_myc"):
+                getattr(L, f).restype = None
+                getattr(L, f).argtypes = [_dp, _dp]
+            L.oracle_centred_column.restype = None
+            L.oracle_centred_column.argtypes = [_dp, C.c_int, _dp]
+            L.oracle_myc_choice.restype = C.c_int
+            L.oracle_myc_choice.argtypes = [_dp]
+            L.oracle_face_flux.restype = C.c_double
+            L.oracle_face_flux.argtypes = [_dp, C.c_double, C.c_int, C.c_double]
+            L.oracle_cell_face_flux.restype = C.c_double
+            L.oracle_cell_face_flux.argtypes = [_dp] + [C.c_int] * 7 + [C.c_double]
+            L.oracle_advect_step.restype = C.c_int
+            L.oracle_advect_step.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.c_double, C.c_int64, _dp]
+            L.oracle_normals.restype = None
+            L.oracle_normals.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp]
+            L.oracle_label.restype = C.c_int64
+            L.oracle_label.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _ip]
+            L.oracle_near_contact.restype = C.c_int
+            L.oracle_near_contact.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
+            L.oracle_near_contact_map.restype = None
+            L.oracle_near_contact_map.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                  C.c_double, _up]
+            L.oracle_near_pairs.restype = C.c_int64
+            L.oracle_near_pairs.argtypes = [_dp, _ip, C.c_int, C.c_int, C.c_int, C.c_int,
+                                            C.c_double, C.c_void_p, C.c_void_p, C.c_int64]
+            L.oracle_recolour.restype = C.c_int
+            L.oracle_recolour.argtypes = [_dp, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                          C.c_int, C.c_int, C.c_double, C.c_int,
+                                          C.POINTER(C.c_int), C.c_void_p, C.c_int]
+            L.oracle_drop_table.restype = None
+            L.oracle_drop_table.argtypes = [_dp, _ip, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                            C.c_double, _dp, _dp]
+            L.oracle_pair_stats.restype = None
+            L.oracle_pair_stats.argtypes = [_dp, C.c_int64, _dp, C.c_int, C.c_int, C.c_double,
+                                            C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp,
+                                            _dp]
+            _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------- PLIC
+
+
+def plic_volume(m, alpha):
+    return lib().oracle_plic_volume(_f64(m), float(alpha))
+
+
+def plic_alpha(m, c):
+    return lib().oracle_plic_alpha(_f64(m), float(c))
+
+
+def youngs(st):
+    out = np.zeros(3)
+    lib().oracle_youngs(_f64(st).ravel(), out)
+    return out
+
+
+def centred_column(st, axis):
+    out = np.zeros(3)
+    lib().oracle_centred_column(_f64(st).ravel(), int(axis), out)
+    return out
+
+
+def myc(st):
+    out = np.zeros(3)
+    lib().oracle_myc(_f64(st).ravel(), out)
+    return out
+
+
+def myc_choice(st):
+    return lib().oracle_myc_choice(_f64(st).ravel())
+
+
+def face_flux(m, alpha, d, s):
+    return lib().oracle_face_flux(_f64(m), float(alpha), int(d), float(s))
+
+
+def cell_face_flux(c, i, j, k, d, s):
+    nz, ny, nx = c.shape
+    return lib().oracle_cell_face_flux(_f64(c), nx, ny, nz, i, j, k, d, float(s))
+
+
+# --------------------------------------------------------------------------- advection
+
+
+def advect_step(c, u, dt, h, step_index):
+    """One step of every field; returns (c_new, clipped[K])."""
+    c = np.array(c, dtype=np.float64, order="C", copy=True)
+    squeeze = c.ndim == 3
+    if squeeze:
+        c = c[None]
+    K, nz, ny, nx = c.shape
+    clipped = np.zeros(K)
+    rc = lib().oracle_advect_step(c, _f64(u), nx, ny, nz, K, float(dt), float(h),
+                                  int(step_index), clipped)
+    if rc != 0:
+        raise MemoryError("oracle_advect_step")
+    return (c[0] if squeeze else c), clipped
+
+
+def advect(c, u, dt, h, steps, first_step=0):
+    clipped = 0.0
+    for s in range(steps):
+        c, cl = advect_step(c, u, dt, h, first_step + s)
+        clipped = clipped + cl
+    return c, clipped
+
+
+def normals(c):
+    nz, ny, nx = c.shape
+    out = np.zeros((nz, ny, nx, 3))
+    lib().oracle_normals(_f64(c), nx, ny, nz, out)
+    return out
+
+
+# --------------------------------------------------------------------------- tagging
+
+
+def label(c, tau=0.0, connectivity=6):
+    nz, ny, nx = c.shape
+    lab = np.zeros(c.shape, dtype=np.int32)
+    n = lib().oracle_label(_f64(c), nx, ny, nz, float(tau), int(connectivity), lab)
+    if n < 0:
+        raise MemoryError("oracle_label")
+    return lab, int(n)
+
+
+def near_contact(c, w=2, tau=0.0):
+    nz, ny, nx = c.shape
+    return bool(lib().oracle_near_contact(_f64(c), nx, ny, nz, int(w), float(tau)))
+
+
+def near_contact_map(c, w=2, tau=0.0):
+    nz, ny, nx = c.shape
+    out = np.zeros(c.shape, dtype=np.uint8)
+    lib().oracle_near_contact_map(_f64(c), nx, ny, nz, int(w), float(tau), out)
+    return out
+
+
+def near_pairs(c, lab, w=2, tau=0.0):
+    nz, ny, nx = c.shape
+    cf = _f64(c)
+    lb = np.ascontiguousarray(lab, dtype=np.int32)
+    n = lib().oracle_near_pairs(cf, lb, nx, ny, nz, int(w), float(tau), None, None, 0)
+    pa = np.zeros(max(n, 1), dtype=np.int32)
+    pb = np.zeros(max(n, 1), dtype=np.int32)
+    lib().oracle_near_pairs(cf, lb, nx, ny, nz, int(w), float(tau),
+                            pa.ctypes.data, pb.ctypes.data, n)
+    return np.stack([pa[:n], pb[:n]], axis=1)
+
+
+def recolour(c, n_active, w=2, tau=0.0, connectivity=6, log_cap=4096):
+    """Steps 1-4; returns (c_new, n_active, n_moved, status, moves[(field,label,target)])."""
+    c = np.array(c, dtype=np.float64, order="C", copy=True)
+    K, nz, ny, nx = c.shape
+    na = C.c_int(int(n_active))
+    nm = C.c_int(0)
+    log = np.full((log_cap, 3), -1, dtype=np.int32)
+    st = lib().oracle_recolour(c, K, C.byref(na), nx, ny, nz, int(w), float(tau),
+                               int(connectivity), C.byref(nm), log.ctypes.data, log_cap)
+    if st == -1:
+        raise MemoryError("oracle_recolour")
+    moves = log[: min(nm.value, log_cap)]
+    return c, na.value, nm.value, st, moves
+
+
+# --------------------------------------------------------------------------- statistics
+
+
+def drop_table(c, lab, n_labels, h=1.0):
+    nz, ny, nx = c.shape
+    vol = np.zeros(max(n_labels, 1))
+    cen = np.zeros((max(n_labels, 1), 3))
+    lib().oracle_drop_table(_f64(c), np.ascontiguousarray(lab, dtype=np.int32), int(n_labels),
+                            nx, ny, nz, float(h), vol, cen)
+    return vol[:n_labels], cen[:n_labels]
+
+
+class PairStats:
+    """Accumulators of the nearest-particle statistics (Section 3)."""
+
+    def __init__(self, n_rbins, dr, n_tbins=150, dtheta=np.pi / 150):
+        self.n_rbins, self.dr, self.n_tbins, self.dtheta = n_rbins, dr, n_tbins, dtheta
+        self.hist_r = np.zeros(n_rbins + 1)
+        self.hist_rt = np.zeros((n_rbins + 1) * n_tbins)
+        self.msum = np.zeros(3)
+        self.rsum = np.zeros(9)
+        self.events = np.zeros(1)
+
+    def add(self, cen, box, vertical_axis=2, tie_tol=0.0):
+        cen = _f64(cen).reshape(-1, 3)
+        lib().oracle_pair_stats(cen, len(cen), _f64(box), int(vertical_axis), self.n_rbins,
+                                float(self.dr), self.n_tbins, float(self.dtheta),
+                                float(tie_tol), self.hist_r, self.hist_rt, self.msum,
+                                self.rsum, self.events)
+        return self
+
+    @property
+    def E(self):
+        return float(self.events[0])
+
+    @property
+    def M(self):
+        return self.msum / self.E
+
+    @property
+    def R(self):
+        return self.rsum.reshape(3, 3) / self.E
+
+    @property
+    def A(self):
+        R = self.R
+        return R - np.trace(R) / 3.0 * np.eye(3)

@@ -1,0 +1,108 @@
+/*
+ * FP64 CPU oracle of the multi-field VoF step (arXiv 2407.07463).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It is a plain, slow,
+ * obviously-correct restatement of what the GPU path computes and shares no
+ * code, header, table or helper with it.
+ *
+ * Grid conventions: fields are C-contiguous [nz][ny][nx] (x fastest), cell
+ * (i,j,k) occupies [i,i+1]x[j,j+1]x[k,k+1] in cell units, tri-periodic.
+ * u[d] holds the velocity on the LOW d-face of each cell.  All reals FP64.
+ */
+#ifndef VOF_ORACLE_H
+#define VOF_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Section 2.2 (PLIC): volume of {x in [0,1]^3 : m.x < alpha}. */
+double oracle_plic_volume(const double m[3], double alpha);
+/* Plane constant alpha with oracle_plic_volume(m, alpha) = c (bisection). */
+double oracle_plic_alpha(const double m[3], double c);
+
+/* Normals from a 3x3x3 stencil st[(k+1)*9 + (j+1)*3 + (i+1)], offsets
+ * i (x), j (y), k (z) in {-1,0,1}.  Normals point out of the c = 1 phase and
+ * are L1-normalised. */
+void oracle_youngs(const double st[27], double m[3]);
+void oracle_centred_column(const double st[27], int axis, double m[3]);
+void oracle_myc(const double st[27], double m[3]);
+/* Youngs candidate and which candidate MYC picked: 0,1,2 = centred column
+ * along x,y,z; 3 = Youngs. */
+int oracle_myc_choice(const double st[27]);
+
+/* Split flux through one face: donor reconstruction (m, alpha), sweep
+ * direction d, Courant number s = u dt / h on the face (signed). */
+double oracle_face_flux(const double m[3], double alpha, int d, double s);
+
+/* Flux through the low d-face of cell (i,j,k) of field c with Courant number
+ * s: donor selection, MYC, alpha and sub-cell volume. */
+double oracle_cell_face_flux(const double *c, int nx, int ny, int nz,
+                             int i, int j, int k, int d, double s);
+
+/* One time step of every field: three split sweeps in the order rotated by
+ * step_index, Weymouth-Yue divergence term with c_c from the start-of-step
+ * field, clip to [0,1] after the third sweep.  c is [K][nz][ny][nx] and is
+ * updated in place; clipped[k] (may be NULL) receives the volume removed by
+ * the clip (negative if added).  Returns 0, or -1 on allocation failure. */
+int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz,
+                       int K, double dt, double h, int64_t step_index,
+                       double *clipped);
+
+/* MYC normal of every cell of one field (3 doubles per cell; zeros for
+ * cells with c <= 0 or c >= 1). */
+void oracle_normals(const double *c, int nx, int ny, int nz, double *m_out);
+
+/* Connected-component labels of {c > tau}, periodic, connectivity 6 or 26,
+ * numbered 1..n in the order of each component's smallest linear index.
+ * Returns n, or -1 on allocation failure. */
+int64_t oracle_label(const double *c, int nx, int ny, int nz, double tau,
+                     int connectivity, int32_t *label);
+
+/* Step 1: 1 if some cell with c <= tau has two opposite cells of its
+ * (2w+1)^3 stencil with c > tau. */
+int oracle_near_contact(const double *c, int nx, int ny, int nz, int w,
+                        double tau);
+/* Per-cell Step 1 indicator (uint8 per cell). */
+void oracle_near_contact_map(const double *c, int nx, int ny, int nz, int w,
+                             double tau, uint8_t *out);
+
+/* Step 3: distinct unordered label pairs (a < b) of opposite stencil cells
+ * around an empty centre, sorted; returns the number found (entries beyond
+ * cap are counted but not stored), or -1 on allocation failure. */
+int64_t oracle_near_pairs(const double *c, const int32_t *label, int nx,
+                          int ny, int nz, int w, double tau, int32_t *pa,
+                          int32_t *pb, int64_t cap);
+
+/* Steps 1-4 on every field active at the start of the call.  Returns 0,
+ * or -4 when some drop found no free field (it stays in place).  Moves are
+ * reported through n_moved and the field count through n_active.  If
+ * move_log is not NULL, (field, label, target) triples are appended
+ * (capacity log_cap triples). */
+int oracle_recolour(double *c, int K, int *n_active, int nx, int ny, int nz,
+                    int w, double tau, int connectivity, int *n_moved,
+                    int32_t *move_log, int log_cap);
+
+/* Drop volume and centroid (minimum-image unwrap about the drop's first
+ * cell) for labels 1..n_labels.  cen is [n_labels][3] (x,y,z). */
+void oracle_drop_table(const double *c, const int32_t *label,
+                       int64_t n_labels, int nx, int ny, int nz, double h,
+                       double *vol, double *cen);
+
+/* Nearest-particle statistics (Section 3): for every particle, its nearest
+ * neighbours under the minimum image (ties within tie_tol share weight
+ * 1/N_i), histograms of r and (r, theta), first and second moment sums.
+ * hist_r has n_rbins+1 entries (last = overflow), hist_rt has
+ * (n_rbins+1)*n_tbins.  Accumulates into the outputs. */
+void oracle_pair_stats(const double *cen, int64_t n, const double box[3],
+                       int vertical_axis, int n_rbins, double dr,
+                       int n_tbins, double dtheta, double tie_tol,
+                       double *hist_r, double *hist_rt, double *msum,
+                       double *rsum, double *events);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
