@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of one multi-field VoF time step (arXiv 2407.07463, Section 2.3).
+
+A step is the whole hot path on one box: three split PLIC advection sweeps of
+every active colour field, then the no-coalescence Steps 1-4 (near-contact
+test on every field, tagging and recolouring when it fires).  The workload is
+256^3 cells, K = 8 colour fields, phi = 0.3 (2347 spheres of radius 8 cells,
+coloured greedily over the fields), a 16-mode solenoidal velocity with
+amplitude 0.5 plus a vertical drift of 1, CFL 0.3.  Metric: cell-field updates
+per second = cells x active fields x steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank advances its own independent box (weak scaling) and
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VoF cell-field updates/s at 256^3 K=8; FP32+learned vs plain FP64 same GPU"
+UNIT = "cell-field updates/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=256, help="cells per axis")
+    p.add_argument("--k", type=int, default=8, help="colour fields")
+    p.add_argument("--phi", type=float, default=0.3)
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--fp64-steps", type=int, default=3, help="steps of the FP64 comparison run")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=64, help="sub-box edge of the oracle sample")
+    return p.parse_args()
+
+
+def workload(n, k, phi, seed):
+    from paper_2407_07463_gb300 import synth
+
+    return synth.make_workload(f"{n}^3 K={k} phi={phi} r=8", n=n, k_capacity=k, phi=phi, radius=8.0,
+                               n_modes=16, amplitude=0.5, drift=1.0, cfl=0.3, steps=100, seed=seed)
+
+
+def workload_desc(wl):
+    return (f"{wl.shape[2]}^3 tri-periodic grid, K={wl.k_capacity} colour fields "
+            f"({wl.k_active} active at t=0), {len(wl.centres)} spheres r=8 cells "
+            f"(phi={wl.c.sum() / np.prod(wl.shape):.3f}), 16-mode solenoidal velocity amp 0.5 + "
+            f"vertical drift 1, CFL 0.3, near-contact w=2 + recolouring every step")
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2407_07463_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM, "fallback 6.8 TB/s"
+
+
+def algorithmic_bytes(cls, n_cells, fields, es):
+    """Minimum DRAM bytes one launch of a kernel class must move (per launch).
+    update: read c_in, read c at the step start (c_c), write c_out per
+    cell-field, plus the sweep's velocity component per cell.
+    find_faces: read c_in per cell-field plus the velocity component.
+    pack_bits: read c per cell-field, write one bit.  near_contact: read and
+    write one bit per cell-field."""
+    if cls == "update":
+        return n_cells * fields * 3 * es + n_cells * es
+    if cls == "find_faces":
+        return n_cells * fields * es + n_cells * es
+    if cls == "pack_bits":
+        return n_cells * fields * (es + 1 / 8)
+    if cls == "near_contact":
+        return n_cells * fields * 2 / 8
+    return None
+
+
+def cpu_sample_rate(wl, edge, steps=1):
+    """Oracle (single thread) on the sub-box [0, edge)^3 of the workload:
+    one advection step of every active field, then Steps 1-4."""
+    import oracle
+
+    sub = np.ascontiguousarray(wl.c[:wl.k_active, :edge, :edge, :edge])
+    u = np.ascontiguousarray(wl.u[:, :edge, :edge, :edge])
+    t0 = time.perf_counter()
+    c = sub
+    na = wl.k_active
+    for s in range(steps):
+        c, _ = oracle.advect_step(c, u, wl.dt, wl.h, s)
+        full = np.zeros((wl.k_capacity,) + c.shape[1:])
+        full[:na] = c[:na]
+        full, na, _, _, _ = oracle.recolour(full, na, w=2)
+        c = full[:na]
+    dt = time.perf_counter() - t0
+    updates = edge ** 3 * wl.k_active * steps
+    return updates / dt, dt, updates
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    wl = workload(args.n, args.k, args.phi, seed=3)
+    edge = min(args.cpu_sample, 48, args.n)
+    for _ in range(args.warmup):
+        cpu_sample_rate(wl, edge)
+    times = []
+    upd = 0
+    for _ in range(args.steps):
+        r, t, u = cpu_sample_rate(wl, edge)
+        times.append(t)
+        upd += u
+    total = sum(times)
+    value = upd / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_desc(wl),
+                       "sample": f"oracle step (advect + Steps 1-4) on the {edge}^3 sub-box"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{edge}^3 x {wl.k_active} fields sub-box of the workload, "
+                                       f"one step per timed step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def timed_steps(torch, ctx, dt, steps):
+    st = ctx.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    rep = ctx.vof_step(dt, steps, report=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), rep
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2407_07463_gb300 import vof
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = workload(args.n, args.k, args.phi, seed=3 + rank)
+    nz, ny, nx = wl.shape
+    N = nx * ny * nz
+    prec = vof.VOF_MIXED if args.precision == "mixed" else vof.VOF_FP64
+    tdt = torch.float32 if prec == vof.VOF_MIXED else torch.float64
+    es = 4 if prec == vof.VOF_MIXED else 8
+    rbins = 2000
+    cfg = vof.make_config(nx, ny, nz, k_capacity=wl.k_capacity, k_active=wl.k_active, precision=prec,
+                          recolour=1, stats_rbins=rbins, stats_dr=0.16)
+    c_d = torch.from_numpy(wl.c).to(dev, tdt).contiguous()
+    u_d = torch.from_numpy(wl.u).to(dev, tdt).contiguous()
+    ctx = vof.Context(cfg, c_d, u_d)
+    torch.cuda.synchronize()
+    if args.warmup:
+        ctx.vof_step(wl.dt, args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region (launch timer on; barrier + synchronize on both sides)
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    ctx.vof_profile_enable(True)
+    ctx.vof_profile_read()
+    if dist:
+        dist.barrier()
+    sampler.start()
+    l0 = ctx.launches
+    ms, rep = timed_steps(torch, ctx, wl.dt, args.steps)
+    launches = ctx.launches - l0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = ctx.vof_profile_read()
+    ctx.vof_profile_enable(False)
+    updates = N * rep["field_steps"]
+    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
+    if dist:
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max, updates_all = float(tmax[0]), float(tsum[0])
+    else:
+        ms_max, updates_all = ms, float(updates)
+    value = updates_all / (ms_max * 1e-3)
+
+    # e2e through the public API with host buffers: per step, pinned H2D of
+    # the step's inputs (c and u), the step, D2H of the result (c)
+    e2e = None
+    if args.e2e_steps > 0:
+        c_h = torch.from_numpy(wl.c).to(tdt).pin_memory()
+        u_h = torch.from_numpy(wl.u).to(tdt).pin_memory()
+        c_out = torch.empty_like(c_h).pin_memory()
+        st = ctx.stream
+        fields0 = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.e2e_steps):
+            c_d.copy_(c_h, non_blocking=True)
+            u_d.copy_(u_h, non_blocking=True)
+            r = ctx.vof_step(wl.dt, 1, report=True)
+            fields0.append(r["field_steps"])
+            c_out.copy_(c_d, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": N * sum(fields0) / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(c_h.numel() * es + u_h.numel() * es),
+               "d2h_bytes_per_step": int(c_out.numel() * es), "steps": args.e2e_steps}
+
+    # FP64 comparison path on the same workload (plain FP64 kernels)
+    fp64 = None
+    if not args.no_fp64 and prec == vof.VOF_MIXED and args.fp64_steps > 0:
+        del ctx
+        torch.cuda.empty_cache()
+        cfg64 = vof.make_config(nx, ny, nz, k_capacity=wl.k_capacity, k_active=wl.k_active,
+                                precision=vof.VOF_FP64, recolour=1, stats_rbins=rbins, stats_dr=0.16)
+        c64 = torch.from_numpy(wl.c).to(dev).contiguous()
+        u64 = torch.from_numpy(wl.u).to(dev).contiguous()
+        ctx64 = vof.Context(cfg64, c64, u64)
+        ctx64.vof_step(wl.dt, 1)
+        ms64, rep64 = timed_steps(torch, ctx64, wl.dt, args.fp64_steps)
+        fp64 = {"value": N * rep64["field_steps"] / (ms64 * 1e-3), "unit": UNIT,
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+        del ctx64, c64, u64
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class
+    hbm, peak_src = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (cnt, tot) = dom
+        fields = rep["field_steps"] / max(args.steps, 1)
+        alg = algorithmic_bytes(name, N, fields, es)
+        traffic = None
+        try:
+            with open(TRAFFIC) as f:
+                tr = json.load(f)
+            if tr.get("source_hash") == src_hash() and name in tr.get("kernels", {}):
+                traffic = tr["kernels"][name]
+        except (OSError, ValueError):
+            pass
+        if alg is not None:
+            ach = alg / (tot / cnt * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": traffic, "kernel": name, "launches": cnt,
+                    "avg_ms": tot / cnt, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src,
+                    "share_of_timed": tot / ms}
+        else:
+            roof = {"bound": "alu", "kernel": name, "launches": cnt, "avg_ms": tot / cnt,
+                    "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": traffic}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+
+        oracle.build()
+        r, t, u = cpu_sample_rate(wl, min(args.cpu_sample, args.n))
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle step (advect + Steps 1-4) of the {min(args.cpu_sample, args.n)}^3 "
+                         f"sub-box, {wl.k_active} active fields ({t:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == vof.VOF_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(wl),
+                       "precision": "mixed (f32, f64 alpha band 1e-3 and clip sums)"
+                       if prec == vof.VOF_MIXED else "fp64",
+                       "normals": "MYC", "l2": "inputs larger than L2 (fields "
+                       f"{wl.k_capacity * N * es / 1e6:.0f} MB)",
+                       "parallelism": f"{world} independent boxes" if world > 1 else "1 box",
+                       "n_active_end": rep["n_active"], "drops_moved": rep["n_moved"],
+                       "near_contact_steps": rep["near_contact_steps"]},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu, "fp64_path": fp64,
+            "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
+    if fp64:
+        line["mixed_over_fp64"] = value / world / fp64["value"]
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

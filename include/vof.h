@@ -1,0 +1,239 @@
+/*
+ * vof.h -- C ABI of the GB300 multi-field VoF library (libvof.so).
+ *
+ * One time step of K colour fields C_i on a tri-periodic uniform grid
+ * (Section 2.3 of "Buoyancy driven motion of non-coalescing inertial drops",
+ * arXiv 2407.07463): geometric PLIC transport of every field (Section 2.2,
+ * Mixed-Youngs-Centred normals, plane-constant inversion, directionally split
+ * fluxes), then the no-coalescence Steps 1-4 (near-contact test, tagging,
+ * tagged near-contact pairs, recolouring), and the nearest-particle
+ * statistics of Section 3 from the tags.
+ *
+ * Conventions shared by every entry point
+ *  - Grids are C-contiguous [nz][ny][nx] (x fastest).  Cell (i,j,k) spans
+ *    [i,i+1]x[j,j+1]x[k,k+1] in cells; positions are in units of h.
+ *  - c is [K][nz][ny][nx]; u is [3][nz][ny][nx], u[d] being the velocity on
+ *    the LOW d-face of the cell.  Element type: double for VOF_FP64, float for
+ *    VOF_MIXED and VOF_MIXED_LEARNED.
+ *  - "_dev" pointers are device memory of the current CUDA device, "_host"
+ *    pointers host memory.  The caller owns every buffer; the library
+ *    allocates no device memory after vof_init (all scratch lives in the
+ *    caller's workspace) and never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Work is enqueued on it; calls that return host values synchronise it.
+ *  - Every call validates its arguments before launching anything and
+ *    returns a vof_status; no C++ exception crosses the ABI.  VOF_ERR_CUDA
+ *    and VOF_ERR_TIMEOUT are sticky: the context must then be destroyed.
+ */
+#ifndef VOF_H
+#define VOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VOF_OK = 0,
+    VOF_ERR_ARG = -1,          /* invalid argument; nothing was launched */
+    VOF_ERR_CUDA = -2,         /* a CUDA call failed (sticky) */
+    VOF_ERR_WORKSPACE = -3,    /* workspace smaller than vof_workspace_size() */
+    VOF_ERR_NO_FREE_FIELD = -4,/* Step 4 found no field for some drop (non-fatal) */
+    VOF_ERR_CFL = -5,          /* max |u| dt / h > 1/2 */
+    VOF_ERR_TIMEOUT = -6,      /* a bounded device wait gave up (sticky) */
+    VOF_ERR_STATE = -7,        /* state blob does not match the context */
+    VOF_ERR_NONFINITE = -8,    /* NaN or Inf in the velocity */
+    VOF_ERR_CAPACITY = -9      /* a fixed-capacity list overflowed */
+} vof_status;
+
+typedef enum {
+    VOF_FP64 = 0,          /* everything in double */
+    VOF_MIXED = 1,         /* float storage, normals and fluxes; double alpha
+                              near c = 0 or 1 and double clipping sums */
+    VOF_MIXED_LEARNED = 2  /* VOF_MIXED with the learned normal estimator */
+} vof_precision;
+
+typedef struct {
+    int32_t nx, ny, nz;      /* cells per axis, each >= 1; nx*ny*nz < 2^31 */
+    int32_t k_capacity;      /* number of colour fields stored (K), 1..16 */
+    int32_t k_active;        /* fields in use at start, N(0), 1..K */
+    int32_t precision;       /* vof_precision */
+    double h;                /* cell size > 0 */
+    int32_t stencil_w;       /* near-contact half width w (2 = 5-cell stencil) */
+    int32_t connectivity;    /* tagging connectivity: 6 or 26 */
+    double tag_tau;          /* a cell belongs to a drop iff c > tag_tau (>= 0) */
+    double alpha_fp64_band;  /* mixed path: alpha in double if c < band or
+                                c > 1 - band */
+    int32_t recolour;        /* 1: run Steps 1-4 after every step of vof_step */
+    int32_t vertical_axis;   /* 0, 1, 2: axis theta is measured from */
+    int32_t stats_rbins;     /* radial bins of the statistics (plus overflow) */
+    int32_t stats_tbins;     /* polar bins over [0, pi] */
+    double stats_dr;         /* radial bin width (length units) */
+} vof_config;
+
+/* Fill `cfg` with defaults: 32^3, K = 1, FP64, h = 1, w = 2, 6-connectivity,
+ * tau = 0, band 1e-3, no recolouring, vertical axis z, 1024 x 150 bins of
+ * width 0.2. */
+vof_status vof_config_default(vof_config *cfg);
+
+typedef struct vof_ctx vof_ctx;
+
+/* Bytes of device workspace vof_init needs for `cfg` (0 if cfg invalid). */
+size_t vof_workspace_size(const vof_config *cfg);
+
+/*
+ * Create a context.  c_dev and u_dev are borrowed for the context's
+ * lifetime (c is updated in place by vof_step / vof_recolour, u is read
+ * only); workspace_dev must hold vof_workspace_size(cfg) bytes and be
+ * 256-byte aligned.  Scans u once (synchronising `stream`): VOF_ERR_NONFINITE
+ * if it holds NaN/Inf.  Fields k >= k_active must be zero.
+ */
+vof_status vof_init(const vof_config *cfg, void *c_dev, const void *u_dev,
+                    void *workspace_dev, size_t workspace_bytes, void *stream,
+                    vof_ctx **out);
+
+/* Re-scan the borrowed velocity after the caller changed it. */
+vof_status vof_set_velocity(vof_ctx *ctx, const void *u_dev);
+
+typedef struct {
+    int64_t steps_done;        /* total steps taken by this context */
+    double clipped_volume;     /* volume removed by clipping during the call */
+    int32_t n_active;          /* active fields N(t) after the call */
+    int32_t n_moved;           /* drops moved by Step 4 during the call */
+    int32_t near_contact_steps;/* steps whose Step 1 fired somewhere */
+    int64_t field_steps;       /* sum over the call's steps of fields advected */
+} vof_step_report;
+
+/*
+ * Advance every active field by `nsteps` steps of size dt (Section 2.2 /
+ * 2.3, the transport equation of each C_i): per step, three split sweeps in
+ * the order (x,y,z), (y,z,x), (z,x,y) by step index mod 3, each with
+ * Mixed-Youngs-Centred normals and PLIC plane constants recomputed from the
+ * current field, face fluxes of the upwind donor's sub-cell, the
+ * Weymouth-Yue term c_c (u_hi - u_lo) with c_c = [c > 1/2] of the step's
+ * start, and a clip to [0,1] after the third sweep.  With cfg.recolour,
+ * Steps 1-4 run after every step (synchronising once per step).
+ * VOF_ERR_CFL if max |u| dt / h > 1/2.  `report` may be NULL.  Asynchronous
+ * when recolouring is off and report is NULL.
+ */
+vof_status vof_step(vof_ctx *ctx, double dt, int32_t nsteps, vof_step_report *report);
+
+/* Step 1 for every active field: flags_host[k] = 1 if field k has a cell
+ * with c <= tau whose (2w+1)^3 stencil holds two opposite cells with
+ * c > tau (Section 2.3, Step 1; caption of figure fig:criterion).
+ * Synchronises.  flags_host has k_capacity entries (inactive fields get 0). */
+vof_status vof_near_contact(vof_ctx *ctx, int32_t *flags_host);
+
+/*
+ * Tagging (Section 2.3, tag.h): label_dev[nz][ny][nx] (int32, caller-owned)
+ * receives 0 for cells with c <= tau and 1..n for the periodic connected
+ * components of {c > tau} of field `field`, numbered in the order of each
+ * component's smallest linear index.  *n_drops_host = n.  Synchronises.
+ */
+vof_status vof_label(vof_ctx *ctx, int32_t field, int32_t *label_dev, int32_t *n_drops_host);
+
+/*
+ * Steps 1-4 on every active field (Section 2.3).  Steps 1-3 are evaluated on
+ * the state at the start of the call; per field, sorted distinct tag pairs
+ * (a < b) mark b as moving unless a or b already moves; moving drops, in
+ * (field, tag) order, go to the smallest active field other than their own
+ * with no occupied cell within Chebyshev distance 2w of the drop (counting
+ * drops already moved into it), else to a newly activated field.  Moving
+ * adds the drop's c to the target field and zeroes it in the source field.
+ * VOF_ERR_NO_FREE_FIELD if some drop found no field with K exhausted (it
+ * stays; the rest of the call completes).  Synchronises.
+ */
+vof_status vof_recolour(vof_ctx *ctx, int32_t *n_moved, int32_t *n_active);
+
+typedef struct {
+    int32_t n_drops;      /* drops in all active fields */
+    double d;             /* equivalent diameter (6 Vbar / pi)^(1/3) */
+    double n_p;           /* number density n_drops / L^3 */
+    double volume;        /* total dispersed volume sum_k sum c h^3 */
+    double events;        /* accumulated events E (one per drop per call) */
+    double M[3];          /* first moment  sum h_ij r / E (accumulated) */
+    double R[9];          /* second moment sum h_ij r r^T / E (accumulated) */
+    double A[9];          /* R - tr(R)/3 delta */
+} vof_stats_out;
+
+/*
+ * Nearest-particle statistics (Section 3): tag every active field, compute
+ * each drop's volume and centroid (minimum image about the drop's first
+ * cell), then for every drop its nearest neighbours among all drops of all
+ * fields under the minimum image (ties within 1e-12 d share h_ij = 1/N_i),
+ * and accumulate the events into histograms over r (stats_rbins bins of
+ * width stats_dr plus an overflow bin) and over (r, theta) with theta the
+ * angle to the vertical axis (stats_tbins bins over [0, pi]), and into the
+ * moment sums.  hist_r_host (stats_rbins + 1 doubles) and hist_rt_host
+ * ((stats_rbins + 1) * stats_tbins doubles, r-major) receive the accumulated
+ * histograms if not NULL.  reset != 0 clears the accumulators first.
+ * Synchronises.
+ */
+vof_status vof_stats(vof_ctx *ctx, int32_t reset, vof_stats_out *out, double *hist_r_host,
+                     double *hist_rt_host);
+
+/* Per-drop table of one field given its labels: vol_dev[n] (double) and
+ * cen_dev[n][3] (double, x y z in [0, L h)).  Section 2.3 (drop properties
+ * by integrating C_i over the cells of a tag).  Asynchronous. */
+vof_status vof_drop_table(vof_ctx *ctx, int32_t field, const int32_t *label_dev,
+                          int32_t n_labels, double *vol_dev, double *cen_dev);
+
+/*
+ * Stateless nearest-particle statistics of n centroids cen_dev[n][3]
+ * (double) in a periodic box box_host[3] (Section 3, eqs. P_nstij, vec_cond,
+ * Ptheta_r): accumulates into hist_r_dev[n_rbins+1], hist_rt_dev
+ * [(n_rbins+1)*n_tbins] and moments_dev[13] = {sum h r (3), sum h r r^T (9),
+ * E}.  Asynchronous on `stream`.
+ */
+vof_status vof_pair_stats(const double *cen_dev, int64_t n, const double *box_host,
+                          int32_t vertical_axis, int32_t n_rbins, double dr, int32_t n_tbins,
+                          double dtheta, double tie_tol, double *hist_r_dev,
+                          double *hist_rt_dev, double *moments_dev, void *stream);
+
+/* PLIC primitives on n independent cells (Section 2.2): volume of
+ * {x in [0,1]^3 : m.x < alpha} and its inverse alpha(m, c).  m is [n][3];
+ * all arrays of `precision`'s element type (double for VOF_FP64).  The mixed
+ * precisions compute alpha in double when c < band or c > 1 - band.
+ * Asynchronous on `stream`. */
+vof_status vof_plic_volume(int32_t precision, const void *m_dev, const void *alpha_dev,
+                           void *v_dev, int64_t n, void *stream);
+vof_status vof_plic_alpha(int32_t precision, const void *m_dev, const void *c_dev,
+                          void *alpha_dev, int64_t n, double band, void *stream);
+
+/* Mixed-Youngs-Centred normal of every cell of `field` (m_dev [N][3] of the
+ * context's element type; zero where c <= 0 or c >= 1).  Asynchronous. */
+vof_status vof_normals(vof_ctx *ctx, int32_t field, void *m_dev);
+
+/* Checkpoint: a self-describing blob of the fields, N(t), the step count
+ * and the statistics accumulators.  vof_state_size gives its size. */
+size_t vof_state_size(const vof_ctx *ctx);
+vof_status vof_get_state(vof_ctx *ctx, void *host_buf, size_t bytes);
+vof_status vof_set_state(vof_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Number of kernel launches this context has issued (instrumentation). */
+int64_t vof_launch_count(const vof_ctx *ctx);
+
+/*
+ * Kernel timing (instrumentation, no counterpart in the paper).  While
+ * enabled, every kernel the context launches is bracketed by a pair of CUDA
+ * events recorded on the context stream (up to 16384 launches; later ones
+ * are not recorded).  vof_profile_read synchronises the stream, writes per
+ * kernel class the number of recorded launches and their summed device time
+ * in milliseconds (arrays of n entries; classes beyond n are dropped) and
+ * clears the record.  vof_profile_class_name names class i (NULL past the
+ * last class).  Events are created at the first enable and destroyed by
+ * vof_destroy; no device memory is allocated.
+ */
+vof_status vof_profile_enable(vof_ctx *ctx, int32_t enable);
+vof_status vof_profile_read(vof_ctx *ctx, int64_t *launches, double *ms, int32_t n);
+const char *vof_profile_class_name(int32_t cls);
+
+const char *vof_status_string(vof_status s);
+void vof_destroy(vof_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOF_H */

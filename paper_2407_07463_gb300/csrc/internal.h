@@ -1,0 +1,103 @@
+// Internal host-side launchers of the GB300 VoF library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+#include <vector>
+
+namespace vof {
+
+// Kernel classes of the launch timer (vof_profile_*).
+enum ProfClass {
+    P_FIND_FACES = 0,
+    P_FACE_FLUX,
+    P_UPDATE,
+    P_PACK_BITS,
+    P_NEAR_CONTACT,
+    P_LABEL,
+    P_PAIRS,
+    P_TOUCH,
+    P_MOVE,
+    P_STATS,
+    P_MISC,
+    P_COUNT
+};
+
+// Optional CUDA-event bracketing of kernel launches on one stream.
+struct Prof {
+    bool on = false;
+    int cap = 0, n = 0, pending = -1;
+    std::vector<cudaEvent_t> ev;  // 2 * cap
+    std::vector<int> cls;         // cap
+    cudaStream_t st = nullptr;
+    void begin(int c) {
+        pending = -1;
+        if (!on || n >= cap) return;
+        cudaEventRecord(ev[2 * n], st);
+        pending = c;
+    }
+    void end() {
+        if (pending < 0) return;
+        cudaEventRecord(ev[2 * n + 1], st);
+        cls[n] = pending;
+        ++n;
+        pending = -1;
+    }
+};
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kPairCap = 1 << 16;     // distinct tagged near-contact pairs per call
+constexpr int kMoveCap = 2048;        // moving drops per recolour call
+constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
+
+struct AdvectArgs;
+cudaError_t advect_steps_fp64(const AdvectArgs& a, int nsteps);
+cudaError_t advect_steps_fp32(const AdvectArgs& a, int nsteps);
+
+cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
+                      cudaStream_t st);
+cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
+                         cudaStream_t st);
+cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
+                        int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
+                        cudaStream_t st, long long* launches);
+cudaError_t tag_pairs(const uint32_t* ncmap_f, const uint32_t* bits_f, const int* label_f, const Dims& g,
+                      int w, int f, unsigned long long* table, int cap, int* overflow, cudaStream_t st);
+cudaError_t compact_pairs(const unsigned long long* table, int cap, unsigned long long* out,
+                          unsigned long long* count, cudaStream_t st);
+
+// Step 4 helpers.  Moving drops are listed per field in increasing label
+// order: mv_label[mv_start[f] .. mv_start[f] + mv_count[f]).
+struct MoveTables {
+    const int* mv_start;   // [K]
+    const int* mv_count;   // [K]
+    const int* mv_label;   // [M]
+    int M;
+};
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, const Dims& g, int K, int n_active,
+                           int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
+                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st);
+cudaError_t recolour_move(void* c, bool fp64, const int* labels, const Dims& g, MoveTables mt,
+                          const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);
+
+// Statistics helpers.
+cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* parent, const Dims& g,
+                      double* S, int n_max, cudaStream_t st);
+cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, double h, int n,
+                          double* vol, double* cen, cudaStream_t st);
+cudaError_t pair_stats(const double* cen, long long n, double bx, double by, double bz, int vaxis,
+                       int n_rbins, double dr, int n_tbins, double dtheta, double tie_tol, double* hist_r,
+                       double* hist_rt, double* moments, cudaStream_t st);
+
+// PLIC primitives and normals (tests and tools).
+cudaError_t plic_volume_batch(bool fp64, const void* m, const void* alpha, void* v, long long n,
+                              cudaStream_t st);
+cudaError_t plic_alpha_batch(bool fp64, const void* m, const void* c, void* alpha, long long n,
+                             double band, cudaStream_t st);
+cudaError_t normals_field(bool fp64, const void* cf, const Dims& g, void* m, cudaStream_t st);
+cudaError_t velocity_scan(bool fp64, const void* u, long long n, double* out2, cudaStream_t st);
+
+}  // namespace vof

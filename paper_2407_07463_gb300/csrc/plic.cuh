@@ -1,0 +1,348 @@
+// PLIC geometry on the device (Section 2.2: geometric VoF with PLIC
+// reconstruction): the volume under a plane in the unit cube, its inverse
+// (the plane constant), Mixed-Youngs-Centred normals and split face fluxes.
+//
+// Volume.  After reflecting negative normal components (x_i -> 1 - x_i) and
+// sorting, 0 <= a <= b <= c.  With A(beta) the area of {(y,z) in [0,1]^2 :
+// b y + c z < beta} -- a piecewise quadratic with breaks at 0, b, c, b + c --
+// the volume is the mean of A over beta in [alpha - a, alpha].  Splitting
+// that interval at the breaks and integrating each quadratic piece with the
+// two-point Gauss-Legendre rule is exact, needs no division by a small
+// product (unlike the inclusion-exclusion closed form of Scardovelli &
+// Zaleski 2000, JCP 164, whose region-3 numerator cancels when a -> 0) and
+// keeps every term non-negative.
+//
+// Inverse.  The volume is convex on [0, S/2] (the cross-section area of a
+// cube grows towards its centre), so the region is located from the volumes
+// at the breaks, the closed-form roots are used in regions 1, 2 and the
+// prism region, Newton on the cubic polynomial (started from the right end of
+// the region, hence monotone) in regions 3 and 4, and one Newton step on the
+// exact piecewise form above polishes every root.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace vof {
+
+template <typename T>
+struct PlicConst;
+template <>
+struct PlicConst<double> {
+    static constexpr double half_inv_sqrt3 = 0.28867513459481288225;  // 1/(2 sqrt 3)
+    static constexpr double tiny = 1e-300;
+    static constexpr int newton_iters = 40;
+    static constexpr double newton_rtol = 4e-16;
+};
+template <>
+struct PlicConst<float> {
+    static constexpr float half_inv_sqrt3 = 0.28867513459481288225f;
+    static constexpr float tiny = 1e-30f;
+    static constexpr int newton_iters = 20;
+    static constexpr float newton_rtol = 2e-7f;
+};
+
+__device__ __forceinline__ double cbrt_t(double v) { return cbrt(v); }
+__device__ __forceinline__ float cbrt_t(float v) { return cbrtf(v); }
+__device__ __forceinline__ double sqrt_t(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
+
+// Area of {(y,z) in [0,1]^2 : a y + b z < beta}, 0 <= a <= b.
+template <typename T>
+__device__ __forceinline__ T area2(T a, T b, T beta) {
+    if (beta <= T(0)) return T(0);
+    T ab = a + b;
+    if (beta >= ab) return T(1);
+    if (a <= T(0)) return beta / b;
+    if (beta < a) return beta * beta / (T(2) * a * b);
+    if (beta < b) return (T(2) * beta - a) / (T(2) * b);
+    T r = ab - beta;
+    return T(1) - r * r / (T(2) * a * b);
+}
+
+// d area2 / d beta.
+template <typename T>
+__device__ __forceinline__ T area2_d(T a, T b, T beta) {
+    T ab = a + b;
+    if (beta <= T(0) || beta >= ab) return T(0);
+    if (a <= T(0)) return T(1) / b;
+    if (beta < a) return beta / (a * b);
+    if (beta < b) return T(1) / b;
+    return (ab - beta) / (a * b);
+}
+
+// Volume for sorted 0 <= a <= b <= c (c > 0), any alpha; piecewise Gauss.
+// The mean of A over [alpha - a, alpha] is taken with the widths of the
+// pieces as they are in floating point (their sum, not a, is the divisor):
+// alpha - a rounds, and dividing by a would leave an error of ulp(alpha)/a.
+template <typename T>
+__device__ T vol_sorted(T a, T b, T c, T alpha) {
+    T lo = alpha - a, hi = alpha;
+    if (a <= PlicConst<T>::tiny || !(hi > lo)) return area2(b, c, alpha);
+    T acc = T(0), wsum = T(0);
+    T u = lo;
+    const T br[4] = {T(0), b, c, b + c};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        T v = q < 4 ? br[q] : hi;
+        if (v > hi) v = hi;
+        if (v > u) {
+            T h = v - u;
+            T mid = T(0.5) * (u + v);
+            T off = h * PlicConst<T>::half_inv_sqrt3;
+            acc += h * (area2(b, c, mid - off) + area2(b, c, mid + off));
+            wsum += h;
+            u = v;
+        }
+    }
+    return T(0.5) * acc / wsum;
+}
+
+template <typename T>
+__device__ T dvol_sorted(T a, T b, T c, T alpha) {
+    T lo = alpha - a, hi = alpha;
+    if (a <= PlicConst<T>::tiny || !(hi > lo)) return area2_d(b, c, alpha);
+    T acc = T(0), wsum = T(0);
+    T u = lo;
+    const T br[4] = {T(0), b, c, b + c};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        T v = q < 4 ? br[q] : hi;
+        if (v > hi) v = hi;
+        if (v > u) {
+            T h = v - u;
+            acc += h * area2_d(b, c, T(0.5) * (u + v));
+            wsum += h;
+            u = v;
+        }
+    }
+    return acc / wsum;
+}
+
+template <typename T>
+__device__ __forceinline__ void sort3(T& a, T& b, T& c) {
+    T t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+}
+
+// Volume of {x in [0,1]^3 : m.x < alpha}.
+template <typename T>
+__device__ T plic_volume(T m0, T m1, T m2, T alpha) {
+    if (m0 < T(0)) { alpha -= m0; m0 = -m0; }
+    if (m1 < T(0)) { alpha -= m1; m1 = -m1; }
+    if (m2 < T(0)) { alpha -= m2; m2 = -m2; }
+    sort3(m0, m1, m2);
+    T S = m0 + m1 + m2;
+    if (S <= T(0)) return alpha > T(0) ? T(1) : T(0);
+    if (alpha <= T(0)) return T(0);
+    if (alpha >= S) return T(1);
+    if (T(2) * alpha > S) return T(1) - vol_sorted(m0, m1, m2, S - alpha);
+    return vol_sorted(m0, m1, m2, alpha);
+}
+
+// Root alpha in (0, S/2] of vol_sorted(a,b,c,alpha) = v, 0 < v <= 1/2.
+template <typename T>
+__device__ T alpha_sorted(T a, T b, T c, T v) {
+    T al;
+    if (a <= PlicConst<T>::tiny) {
+        // plane parallel to one axis: the 2D area function
+        if (b <= PlicConst<T>::tiny) return c * v;
+        T t = sqrt_t(T(2) * b * c * v);
+        if (t < b) return t;
+        return c * v + T(0.5) * b;
+    }
+    T bc = b * c;
+    T Va = a * a / (T(6) * bc);
+    if (v <= Va) {
+        al = cbrt_t(T(6) * a * bc * v);
+    } else {
+        T Vb = (b * b - a * b + a * a / T(3)) / (T(2) * bc);
+        if (v <= Vb) {
+            T disc = T(8) * bc * v - a * a / T(3);
+            al = T(0.5) * (a + sqrt_t(disc > T(0) ? disc : T(0)));
+        } else {
+            T ab = a + b;
+            T S = ab + c;
+            T hi;
+            bool prism = c >= ab;
+            if (prism && v >= ab / (T(2) * c)) {
+                al = c * v + T(0.5) * ab;
+                hi = T(-1);
+            } else {
+                hi = prism ? ab : T(0.5) * S;
+            }
+            if (hi > T(0)) {
+                // Newton on 6abc V = al^3 - (al-a)^3 - (al-b)^3 - [(al-c)^3]
+                T rhs = T(6) * a * bc * v;
+                al = hi;
+                for (int it = 0; it < PlicConst<T>::newton_iters; ++it) {
+                    T da = al - a, db = al - b, dc = al - c;
+                    T f = al * al * al - da * da * da - db * db * db - rhs;
+                    T fp = al * al - da * da - db * db;
+                    if (dc > T(0)) {
+                        f -= dc * dc * dc;
+                        fp -= dc * dc;
+                    }
+                    fp *= T(3);
+                    if (!(fp > T(0))) break;
+                    T stp = f / fp;
+                    al -= stp;
+                    if (al < b) { al = b; break; }
+                    if (fabs(stp) <= PlicConst<T>::newton_rtol * al) break;
+                }
+            }
+        }
+    }
+    // polish on the exact piecewise form
+    T S = a + b + c;
+    T dv = dvol_sorted(a, b, c, al);
+    if (dv > T(0)) {
+        T nal = al - (vol_sorted(a, b, c, al) - v) / dv;
+        if (nal > T(0) && nal <= T(0.5) * S) al = nal;
+    }
+    return al;
+}
+
+// Plane constant alpha with plic_volume(m, alpha) = cv.
+template <typename T>
+__device__ T plic_alpha(T m0, T m1, T m2, T cv) {
+    T off = T(0);
+    if (m0 < T(0)) { off += m0; m0 = -m0; }
+    if (m1 < T(0)) { off += m1; m1 = -m1; }
+    if (m2 < T(0)) { off += m2; m2 = -m2; }
+    sort3(m0, m1, m2);
+    T S = m0 + m1 + m2;
+    if (cv <= T(0)) return off;
+    if (cv >= T(1)) return off + S;
+    bool flip = cv > T(0.5);
+    T v = flip ? T(1) - cv : cv;
+    T al = alpha_sorted(m0, m1, m2, v);
+    if (flip) al = S - al;
+    return al + off;
+}
+
+// Mixed precision: alpha in double inside the band c < band or c > 1-band.
+__device__ __forceinline__ float plic_alpha_banded(float m0, float m1, float m2, float cv,
+                                                   float band) {
+    if (cv < band || cv > 1.f - band)
+        return (float)plic_alpha<double>((double)m0, (double)m1, (double)m2, (double)cv);
+    return plic_alpha<float>(m0, m1, m2, cv);
+}
+__device__ __forceinline__ double plic_alpha_banded(double m0, double m1, double m2, double cv,
+                                                    double) {
+    return plic_alpha<double>(m0, m1, m2, cv);
+}
+
+// ---------------------------------------------------------------------------
+// Normals.  Stencil st[(k+1)*9 + (j+1)*3 + (i+1)], offsets i (x), j (y), k (z).
+
+#define VOF_ST(st, i, j, k) ((st)[((k) + 1) * 9 + ((j) + 1) * 3 + ((i) + 1)])
+
+template <typename T>
+__device__ __forceinline__ void youngs_raw(const T* st, T y[3]) {
+    const T W[3] = {T(1), T(2), T(1)};
+    T yx = T(0), yy = T(0), yz = T(0);
+#pragma unroll
+    for (int b = -1; b <= 1; ++b)
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            T w = W[a + 1] * W[b + 1];
+            yx += w * (VOF_ST(st, -1, a, b) - VOF_ST(st, 1, a, b));
+            yy += w * (VOF_ST(st, a, -1, b) - VOF_ST(st, a, 1, b));
+            yz += w * (VOF_ST(st, a, b, -1) - VOF_ST(st, a, b, 1));
+        }
+    y[0] = yx;
+    y[1] = yy;
+    y[2] = yz;
+}
+
+template <typename T>
+__device__ __forceinline__ T l1norm(const T v[3]) {
+    return fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ T st_axis(const T* st, int axis, int t, int p, int q) {
+    // p along the lower of the two other axes, q along the higher
+    if (axis == 0) return VOF_ST(st, t, p, q);
+    if (axis == 1) return VOF_ST(st, p, t, q);
+    return VOF_ST(st, p, q, t);
+}
+
+// Centred-column candidate along `axis` (not normalised).
+template <typename T>
+__device__ __forceinline__ void centred_column(const T* st, int axis, const T y[3], T m[3]) {
+    T H[3][3];
+#pragma unroll
+    for (int p = -1; p <= 1; ++p)
+#pragma unroll
+        for (int q = -1; q <= 1; ++q)
+            H[p + 1][q + 1] = st_axis(st, axis, -1, p, q) + st_axis(st, axis, 0, p, q) +
+                              st_axis(st, axis, 1, p, q);
+    int b = axis == 0 ? 1 : 0;
+    int c = axis == 2 ? 1 : 2;
+    m[b] = (H[0][1] - H[2][1]) * T(0.5);
+    m[c] = (H[1][0] - H[1][2]) * T(0.5);
+    m[axis] = y[axis] < T(0) ? T(-1) : T(1);
+}
+
+// Mixed-Youngs-Centred normal (L1-normalised, pointing out of the c = 1
+// phase).  Among the three centred-column candidates the one with the
+// largest own-axis component |m_a|/|m|_1 is kept (ties to the lower axis);
+// the Youngs normal (average of the eight vertex gradients) replaces it when
+// its largest |component|/|m|_1 is strictly smaller -- saturated columns make
+// a centred-column normal look more grid-aligned than it is.
+template <typename T>
+__device__ __forceinline__ void myc_normal(const T* st, T m[3]) {
+    T y[3];
+    youngs_raw(st, y);
+    T best[3] = {T(0), T(0), T(0)};
+    T best_own = T(-1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T r[3];
+        centred_column(st, a, y, r);
+        T own = fabs(r[a]) / l1norm(r);
+        if (own > best_own) {
+            best_own = own;
+            best[0] = r[0];
+            best[1] = r[1];
+            best[2] = r[2];
+        }
+    }
+    T ny = l1norm(y);
+    if (ny >= T(1e-30)) {
+        T ymax = fabs(y[0]);
+        if (fabs(y[1]) > ymax) ymax = fabs(y[1]);
+        if (fabs(y[2]) > ymax) ymax = fabs(y[2]);
+        if (ymax / ny < best_own) {
+            m[0] = y[0] / ny;
+            m[1] = y[1] / ny;
+            m[2] = y[2] / ny;
+            return;
+        }
+    }
+    T n = l1norm(best);
+    m[0] = best[0] / n;
+    m[1] = best[1] / n;
+    m[2] = best[2] / n;
+}
+
+// Flux through a face of the donor whose reconstruction is (m, alpha); s is
+// the signed Courant number.  The swept sub-cell x_d in [1-s,1] (s > 0) or
+// [0,|s|] (s < 0) is mapped onto the unit cube: m_d -> m_d |s|,
+// alpha -> alpha - m_d x0.
+template <typename T>
+__device__ __forceinline__ T face_flux(const T m[3], T alpha, int d, T s) {
+    T as = fabs(s);
+    T x0 = s > T(0) ? T(1) - s : T(0);
+    T md = m[d];
+    T mm[3] = {m[0], m[1], m[2]};
+    mm[d] = md * as;
+    T a2 = alpha - md * x0;
+    return s * plic_volume(mm[0], mm[1], mm[2], a2);
+}
+
+}  // namespace vof

@@ -1,0 +1,380 @@
+// Step 4 (recolouring) kernels, drop table and nearest-particle statistics
+// (Section 2.3 Step 4; Section 3), plus the stateless PLIC primitives.
+#include "common.cuh"
+#include "internal.h"
+#include "plic.cuh"
+
+namespace vof {
+
+// --------------------------------------------------------------------------
+// Step 4
+
+// Index of label l among field f's moving drops, or -1.
+__device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) {
+    int lo = mt.mv_start[f], n = mt.mv_count[f];
+    int a = 0, b = n - 1;
+    while (a <= b) {
+        int mid = (a + b) >> 1;
+        int v = mt.mv_label[lo + mid];
+        if (v == l) return lo + mid;
+        if (v < l) a = mid + 1;
+        else b = mid - 1;
+    }
+    return -1;
+}
+
+// For every cell of a moving drop m: the fields (other than its own) with an
+// occupied cell within Chebyshev distance `reach`, and the other moving
+// drops with a cell within that distance.
+__global__ void k_touch(const int* __restrict__ labels, const uint32_t* __restrict__ bits, Dims g,
+                        int n_active, int reach, MoveTables mt, const int* __restrict__ mv_fields,
+                        int n_mv_fields, unsigned* __restrict__ touch, unsigned* __restrict__ conflict,
+                        int Mw) {
+    long long total = (long long)n_mv_fields * g.N;
+    long long per_field_words = (long long)g.rows * g.W;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int fi = (int)(t / g.N);
+        int x = (int)(t - (long long)fi * g.N);
+        int f = mv_fields[fi];
+        int l = labels[(size_t)f * g.N + x];
+        if (l == 0) continue;
+        int m = moving_index(mt, f, l);
+        if (m < 0) continue;
+        int i, j, k;
+        decode(x, g, i, j, k);
+        unsigned tmask = 0;
+        for (int dz = -reach; dz <= reach; ++dz) {
+            int kk = wrapi(k + dz, g.nz);
+            for (int dy = -reach; dy <= reach; ++dy) {
+                int jj = wrapi(j + dy, g.ny);
+                int row = kk * g.ny + jj;
+                for (int dx = -reach; dx <= reach; ++dx) {
+                    int ii = wrapi(i + dx, g.nx);
+                    for (int n = 0; n < n_active; ++n) {
+                        if (n == f || ((tmask >> n) & 1u)) continue;
+                        if (bit_at(bits + (size_t)n * per_field_words, g.W, row, ii)) tmask |= 1u << n;
+                    }
+                    int y = cell(ii, jj, kk, g);
+                    for (int q = 0; q < n_mv_fields; ++q) {
+                        int f2 = mv_fields[q];
+                        int l2 = labels[(size_t)f2 * g.N + y];
+                        if (l2 == 0) continue;
+                        int m2 = moving_index(mt, f2, l2);
+                        if (m2 < 0 || m2 == m) continue;
+                        unsigned bitm = 1u << (m2 & 31);
+                        unsigned* wd = conflict + (size_t)m * Mw + (m2 >> 5);
+                        if (!(*wd & bitm)) atomicOr(wd, bitm);
+                    }
+                }
+            }
+        }
+        if (tmask) atomicOr(touch + m, tmask);
+    }
+}
+
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, const Dims& g, int K, int n_active,
+                           int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
+                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st) {
+    long long total = (long long)n_mv_fields * g.N;
+    k_touch<<<grid_for(total, 128), 128, 0, st>>>(labels, bits, g, n_active, reach, mt, mv_fields,
+                                                   n_mv_fields, touch, conflict, Mw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_move(T* c, const int* __restrict__ labels, Dims g, MoveTables mt,
+                       const int* __restrict__ mv_fields, int n_mv_fields, const int* __restrict__ target) {
+    long long total = (long long)n_mv_fields * g.N;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int fi = (int)(t / g.N);
+        int x = (int)(t - (long long)fi * g.N);
+        int f = mv_fields[fi];
+        int l = labels[(size_t)f * g.N + x];
+        if (l == 0) continue;
+        int m = moving_index(mt, f, l);
+        if (m < 0) continue;
+        int tg = target[m];
+        if (tg < 0) continue;
+        T v = c[(size_t)f * g.N + x];
+        c[(size_t)tg * g.N + x] += v;
+        c[(size_t)f * g.N + x] = T(0);
+    }
+}
+
+cudaError_t recolour_move(void* c, bool fp64, const int* labels, const Dims& g, MoveTables mt,
+                          const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st) {
+    long long total = (long long)n_mv_fields * g.N;
+    if (fp64)
+        k_move<double><<<grid_for(total, 256), 256, 0, st>>>((double*)c, labels, g, mt, mv_fields,
+                                                            n_mv_fields, target);
+    else
+        k_move<float><<<grid_for(total, 256), 256, 0, st>>>((float*)c, labels, g, mt, mv_fields,
+                                                           n_mv_fields, target);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Drop table: volume and centroid by integrating c over the cells of each
+// tag, offsets taken under the minimum image about the tag's root (its
+// smallest linear index).
+
+template <typename T>
+__global__ void k_drop_sums(const T* __restrict__ cf, const int* __restrict__ label_f,
+                            const int* __restrict__ parent, Dims g, double* __restrict__ S, int n_max) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        int l = label_f[x];
+        if (l <= 0 || l > n_max) continue;
+        int r = parent[x];
+        int i, j, k, ri, rj, rk;
+        decode(x, g, i, j, k);
+        decode(r, g, ri, rj, rk);
+        int d0 = i - ri, d1 = j - rj, d2 = k - rk;
+        if (2 * d0 >= g.nx) d0 -= g.nx;
+        if (2 * d0 < -g.nx) d0 += g.nx;
+        if (2 * d1 >= g.ny) d1 -= g.ny;
+        if (2 * d1 < -g.ny) d1 += g.ny;
+        if (2 * d2 >= g.nz) d2 -= g.nz;
+        if (2 * d2 < -g.nz) d2 += g.nz;
+        double v = (double)cf[x];
+        double* s = S + 4 * (size_t)(l - 1);
+        atomicAdd(s + 0, v);
+        if (d0) atomicAdd(s + 1, v * (double)d0);
+        if (d1) atomicAdd(s + 2, v * (double)d1);
+        if (d2) atomicAdd(s + 3, v * (double)d2);
+    }
+}
+
+cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* parent, const Dims& g,
+                      double* S, int n_max, cudaStream_t st) {
+    if (fp64)
+        k_drop_sums<double><<<grid_for(g.N, 256), 256, 0, st>>>((const double*)cf, label_f, parent, g, S, n_max);
+    else
+        k_drop_sums<float><<<grid_for(g.N, 256), 256, 0, st>>>((const float*)cf, label_f, parent, g, S, n_max);
+    return cudaGetLastError();
+}
+
+__global__ void k_drop_finalize(const double* __restrict__ S, const int* __restrict__ root_of, Dims g,
+                                double h, int n, double* __restrict__ vol, double* __restrict__ cen) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const double* s = S + 4 * (size_t)l;
+        int r = root_of[l];
+        int rc[3];
+        decode(r, g, rc[0], rc[1], rc[2]);
+        int L[3] = {g.nx, g.ny, g.nz};
+        vol[l] = s[0] * h * h * h;
+        for (int a = 0; a < 3; ++a) {
+            double p = ((double)rc[a] + 0.5 + s[1 + a] / s[0]) * h;
+            double Lh = (double)L[a] * h;
+            p = fmod(p, Lh);
+            if (p < 0.0) p += Lh;
+            if (p >= Lh) p = 0.0;
+            cen[3 * (size_t)l + a] = p;
+        }
+    }
+}
+
+cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, double h, int n,
+                          double* vol, double* cen, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_drop_finalize<<<grid_for(n, 128), 128, 0, st>>>(S, root_of, g, h, n, vol, cen);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Nearest-particle statistics (Section 3, eq. P_nstij with h_ij = 1/N_i for
+// the N_i equidistant nearest neighbours; histograms of eqs. vec_cond and
+// Ptheta_r; moments M and R of Section 4).
+
+__device__ __forceinline__ double min_image(double t, double L) {
+    if (t > 0.5 * L) t -= L;
+    if (t < -0.5 * L) t += L;
+    return t;
+}
+
+__global__ void __launch_bounds__(128) k_pair_stats(const double* __restrict__ cen, long long n, double bx,
+                                                    double by, double bz, int vaxis, int n_rbins, double dr,
+                                                    int n_tbins, double dtheta, double tie_tol,
+                                                    double* __restrict__ hist_r, double* __restrict__ hist_rt,
+                                                    double* __restrict__ moments) {
+    double loc[13];
+    for (int q = 0; q < 13; ++q) loc[q] = 0.0;
+    double box[3] = {bx, by, bz};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (n < 2) break;
+        double ci[3] = {cen[3 * i], cen[3 * i + 1], cen[3 * i + 2]};
+        double dmin = INFINITY;
+        for (long long j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r0 = min_image(cen[3 * j] - ci[0], box[0]);
+            double r1 = min_image(cen[3 * j + 1] - ci[1], box[1]);
+            double r2 = min_image(cen[3 * j + 2] - ci[2], box[2]);
+            double dd = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+            if (dd < dmin) dmin = dd;
+        }
+        int ni = 0;
+        for (long long j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r0 = min_image(cen[3 * j] - ci[0], box[0]);
+            double r1 = min_image(cen[3 * j + 1] - ci[1], box[1]);
+            double r2 = min_image(cen[3 * j + 2] - ci[2], box[2]);
+            double dd = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+            if (dd - dmin <= tie_tol) ++ni;
+        }
+        double wgt = 1.0 / (double)ni;
+        for (long long j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3];
+            r[0] = min_image(cen[3 * j] - ci[0], box[0]);
+            r[1] = min_image(cen[3 * j + 1] - ci[1], box[1]);
+            r[2] = min_image(cen[3 * j + 2] - ci[2], box[2]);
+            double dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            if (!(dd - dmin <= tie_tol)) continue;
+            int kr = (int)floor(dd / dr);
+            if (kr > n_rbins || kr < 0) kr = n_rbins;
+            double ct = dd > 0.0 ? r[vaxis] / dd : 1.0;
+            if (ct > 1.0) ct = 1.0;
+            if (ct < -1.0) ct = -1.0;
+            int kt = (int)floor(acos(ct) / dtheta);
+            if (kt >= n_tbins) kt = n_tbins - 1;
+            if (kt < 0) kt = 0;
+            atomicAdd(hist_r + kr, wgt);
+            atomicAdd(hist_rt + (size_t)kr * n_tbins + kt, wgt);
+            for (int a = 0; a < 3; ++a) {
+                loc[a] += wgt * r[a];
+                for (int b = 0; b < 3; ++b) loc[3 + 3 * a + b] += wgt * r[a] * r[b];
+            }
+        }
+        loc[12] += 1.0;
+    }
+    // block reduction of the 13 sums
+    __shared__ double red[13][4];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 13; ++q) {
+        double v = loc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 13) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        if (v != 0.0) atomicAdd(moments + threadIdx.x, v);
+    }
+}
+
+cudaError_t pair_stats(const double* cen, long long n, double bx, double by, double bz, int vaxis,
+                       int n_rbins, double dr, int n_tbins, double dtheta, double tie_tol, double* hist_r,
+                       double* hist_rt, double* moments, cudaStream_t st) {
+    if (n < 2) return cudaSuccess;
+    k_pair_stats<<<grid_for(n, 128), 128, 0, st>>>(cen, n, bx, by, bz, vaxis, n_rbins, dr, n_tbins, dtheta,
+                                                    tie_tol, hist_r, hist_rt, moments);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// PLIC primitives, normals, velocity scan
+
+template <typename T>
+__global__ void k_plic_volume(const T* __restrict__ m, const T* __restrict__ alpha, T* __restrict__ v,
+                              long long n) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        v[t] = plic_volume<T>(m[3 * t], m[3 * t + 1], m[3 * t + 2], alpha[t]);
+}
+
+template <typename T>
+__global__ void k_plic_alpha(const T* __restrict__ m, const T* __restrict__ c, T* __restrict__ alpha,
+                             long long n, T band) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        alpha[t] = plic_alpha_banded(m[3 * t], m[3 * t + 1], m[3 * t + 2], c[t], band);
+}
+
+cudaError_t plic_volume_batch(bool fp64, const void* m, const void* alpha, void* v, long long n,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (fp64)
+        k_plic_volume<double><<<grid_for(n, 128), 128, 0, st>>>((const double*)m, (const double*)alpha,
+                                                               (double*)v, n);
+    else
+        k_plic_volume<float><<<grid_for(n, 128), 128, 0, st>>>((const float*)m, (const float*)alpha,
+                                                              (float*)v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t plic_alpha_batch(bool fp64, const void* m, const void* c, void* alpha, long long n,
+                             double band, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (fp64)
+        k_plic_alpha<double><<<grid_for(n, 128), 128, 0, st>>>((const double*)m, (const double*)c,
+                                                              (double*)alpha, n, band);
+    else
+        k_plic_alpha<float><<<grid_for(n, 128), 128, 0, st>>>((const float*)m, (const float*)c,
+                                                             (float*)alpha, n, (float)band);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_normals(const T* __restrict__ cf, Dims g, T* __restrict__ m) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        T r[3] = {T(0), T(0), T(0)};
+        if (vclass(cf[x]) == 1) {
+            int i, j, k;
+            decode(x, g, i, j, k);
+            T st[27];
+            int is[3] = {wrapi(i - 1, g.nx), i, wrapi(i + 1, g.nx)};
+            int js[3] = {wrapi(j - 1, g.ny), j, wrapi(j + 1, g.ny)};
+            int ks[3] = {wrapi(k - 1, g.nz), k, wrapi(k + 1, g.nz)};
+            for (int c = 0; c < 3; ++c)
+                for (int b = 0; b < 3; ++b)
+                    for (int a = 0; a < 3; ++a) st[c * 9 + b * 3 + a] = cf[cell(is[a], js[b], ks[c], g)];
+            myc_normal(st, r);
+        }
+        m[3 * (size_t)x] = r[0];
+        m[3 * (size_t)x + 1] = r[1];
+        m[3 * (size_t)x + 2] = r[2];
+    }
+}
+
+cudaError_t normals_field(bool fp64, const void* cf, const Dims& g, void* m, cudaStream_t st) {
+    if (fp64)
+        k_normals<double><<<grid_for(g.N, 128), 128, 0, st>>>((const double*)cf, g, (double*)m);
+    else
+        k_normals<float><<<grid_for(g.N, 128), 128, 0, st>>>((const float*)cf, g, (float*)m);
+    return cudaGetLastError();
+}
+
+// out2[0] = max |u|, out2[1] = 1 if any non-finite value (both as double).
+template <typename T>
+__global__ void k_vscan(const T* __restrict__ u, long long n, unsigned long long* __restrict__ out) {
+    double mx = 0.0;
+    unsigned bad = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        double v = (double)u[t];
+        if (!isfinite(v)) bad = 1;
+        else mx = fmax(mx, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        bad |= __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(mx));  // non-negative doubles order as ints
+        if (bad) atomicOr(out + 1, 1ull);
+    }
+}
+
+cudaError_t velocity_scan(bool fp64, const void* u, long long n, double* out2, cudaStream_t st) {
+    cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+    if (fp64)
+        k_vscan<double><<<grid_for(n, 256), 256, 0, st>>>((const double*)u, n, (unsigned long long*)out2);
+    else
+        k_vscan<float><<<grid_for(n, 256), 256, 0, st>>>((const float*)u, n, (unsigned long long*)out2);
+    return cudaGetLastError();
+}
+
+}  // namespace vof

@@ -1,0 +1,329 @@
+// Occupancy bits, near-contact test, tagging and tagged near-contact pairs
+// (Section 2.3, Steps 1-3; tag.h).
+//
+// Occupancy of every field is packed one bit per cell, rows of ceil(nx/32)
+// words: Step 1 then reads 1/32 (FP32) or 1/64 (FP64) of the bytes of c and
+// tests 32 cells per 32-bit word with shifts and ANDs.  Tagging is a
+// union-find over the occupied cells (links always to the smaller index, so
+// each component's root is its smallest linear index) followed by a prefix
+// sum over the roots, which yields exactly the numbering of a flood fill in
+// linear-index order.
+#include "common.cuh"
+#include "internal.h"
+
+namespace vof {
+
+// --------------------------------------------------------------------------
+// occupancy bits
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack_bits(const T* __restrict__ c, uint32_t* __restrict__ bits,
+                                                   Dims g, int K, T tau) {
+    long long words = (long long)K * g.rows * g.W;
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    long long per_field = (long long)g.rows * g.W;
+    for (long long wd = warp; wd < words; wd += nwarps) {
+        int f = (int)(wd / per_field);
+        long long rem = wd - (long long)f * per_field;
+        int row = (int)(rem / g.W);
+        int w = (int)(rem - (long long)row * g.W);
+        int x = w * 32 + lane;
+        bool v = x < g.nx && c[(size_t)f * g.N + (size_t)row * g.nx + x] > tau;
+        unsigned m = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) bits[wd] = m;
+    }
+}
+
+cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
+                      cudaStream_t st) {
+    long long words = (long long)K * g.rows * g.W;
+    int blocks = grid_for(words * 32, 256);
+    if (fp64)
+        k_pack_bits<double><<<blocks, 256, 0, st>>>((const double*)c, bits, g, K, tau);
+    else
+        k_pack_bits<float><<<blocks, 256, 0, st>>>((const float*)c, bits, g, K, (float)tau);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Step 1: near contact.  For every cell with c <= tau, is there an offset
+// delta in [-w,w]^3 \ {0} with both cells x + delta and x - delta occupied?
+// One offset per opposite pair: the first nonzero of (dz, dy, dx) positive.
+
+__global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict__ bits,
+                                                      uint32_t* __restrict__ ncmap,
+                                                      int* __restrict__ flags, Dims g, int K, int w) {
+    long long per_field = (long long)g.rows * g.W;
+    long long words = (long long)K * per_field;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words; idx += stride) {
+        int f = (int)(idx / per_field);
+        long long rem = idx - (long long)f * per_field;
+        int row = (int)(rem / g.W);
+        int wi = (int)(rem - (long long)row * g.W);
+        int j = row % g.ny, k = row / g.ny;
+        const uint32_t* fb = bits + (size_t)f * per_field;
+        uint32_t centre = fb[(size_t)row * g.W + wi];
+        uint32_t valid = (wi == g.W - 1 && (g.nx & 31)) ? ((1u << (g.nx & 31)) - 1u) : 0xffffffffu;
+        uint32_t empty = ~centre & valid;
+        uint32_t acc = 0;
+        int x0 = wi * 32;
+        if (empty) {
+            for (int dz = 0; dz <= w; ++dz) {
+                int ka = wrapi(k + dz, g.nz), kb = wrapi(k - dz, g.nz);
+                for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy) {
+                    int ja = wrapi(j + dy, g.ny), jb = wrapi(j - dy, g.ny);
+                    const uint32_t* ra = fb + (size_t)(ka * g.ny + ja) * g.W;
+                    const uint32_t* rb = fb + (size_t)(kb * g.ny + jb) * g.W;
+                    int dx0 = (dz == 0 && dy == 0) ? 1 : -w;
+                    for (int dx = dx0; dx <= w; ++dx) {
+                        acc |= row_window(ra, g.W, g.nx, x0 + dx) & row_window(rb, g.W, g.nx, x0 - dx);
+                    }
+                    if ((acc & empty) == empty) break;
+                }
+                if ((acc & empty) == empty) break;
+            }
+        }
+        uint32_t res = acc & empty;
+        if (ncmap) ncmap[idx] = res;
+        if (res) atomicOr(&flags[f], 1);
+    }
+}
+
+cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
+                         cudaStream_t st) {
+    long long words = (long long)K * g.rows * g.W;
+    k_near_contact<<<grid_for(words, 256), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Tagging (connected components, periodic)
+
+__global__ void k_ccl_init(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        int i = x % g.nx, row = x / g.nx;
+        parent[x] = bit_at(bits_f, g.W, row, i) ? x : -1;
+    }
+}
+
+__device__ __forceinline__ int find_root(const int* parent, int x) {
+    int p = __ldcg(parent + x);
+    while (p != x) {
+        x = p;
+        p = __ldcg(parent + x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void unite(int* parent, int a, int b) {
+    while (true) {
+        a = find_root(parent, a);
+        b = find_root(parent, b);
+        if (a == b) return;
+        if (a < b) {
+            int t = a;
+            a = b;
+            b = t;
+        }
+        int old = atomicMin(parent + a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+__global__ void k_ccl_merge(const uint32_t* __restrict__ bits_f, int* parent, Dims g, int conn) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(x, g, i, j, k);
+        if (!bit_at(bits_f, g.W, k * g.ny + j, i)) continue;
+        for (int dz = -1; dz <= 0; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    // backward half of the neighbourhood
+                    bool back = dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
+                    if (!back) continue;
+                    int nnz = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (conn == 6 && nnz != 1) continue;
+                    int ii = wrapi(i + dx, g.nx), jj = wrapi(j + dy, g.ny), kk = wrapi(k + dz, g.nz);
+                    if (!bit_at(bits_f, g.W, kk * g.ny + jj, ii)) continue;
+                    unite(parent, x, cell(ii, jj, kk, g));
+                }
+    }
+}
+
+__global__ void k_ccl_flatten(int* parent, int N) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        if (parent[x] >= 0) parent[x] = find_root(parent, x);
+    }
+}
+
+// Per block of 1024 cells: rank of each root among the block's roots.
+__global__ void __launch_bounds__(1024) k_ccl_count(const int* __restrict__ parent, int* __restrict__ rank,
+                                                    int* __restrict__ block_tot, int N) {
+    __shared__ int warp_tot[32];
+    int x = blockIdx.x * 1024 + threadIdx.x;
+    bool root = x < N && parent[x] == x;
+    unsigned m = __ballot_sync(0xffffffffu, root);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[wid] = __popc(m);
+    __syncthreads();
+    if (wid == 0) {
+        int v = warp_tot[lane];
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        warp_tot[lane] = incl - v;
+        if (lane == 31) block_tot[blockIdx.x] = incl;
+    }
+    __syncthreads();
+    if (root) rank[x] = warp_tot[wid] + __popc(m & ((1u << lane) - 1u));
+}
+
+// Exclusive scan of n block totals in one block; off[n] = total.
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ tot, int* __restrict__ off,
+                                                      int n, int* total_out) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < n ? tot[i] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int s = wsum[lane];
+            int si = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) si += t;
+            }
+            wsum[lane] = si - s;
+        }
+        __syncthreads();
+        int excl = carry + wsum[wid] + incl - v;
+        if (i < n) off[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        off[n] = carry;
+        if (total_out) *total_out = carry;
+    }
+}
+
+__global__ void k_ccl_relabel(const int* __restrict__ parent, const int* __restrict__ rank,
+                              const int* __restrict__ off, int* __restrict__ label, int* __restrict__ root_of,
+                              int root_cap, int N) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        int r = parent[x];
+        int l = 0;
+        if (r >= 0) {
+            l = off[r >> 10] + rank[r] + 1;
+            if (r == x && root_of && l <= root_cap) root_of[l - 1] = x;
+        }
+        label[x] = l;
+    }
+}
+
+cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
+                        int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
+                        cudaStream_t st, long long* launches) {
+    int nb = (g.N + 1023) / 1024;
+    int blocks = grid_for(g.N, 256);
+    k_ccl_init<<<blocks, 256, 0, st>>>(bits_f, parent, g);
+    k_ccl_merge<<<blocks, 256, 0, st>>>(bits_f, parent, g, conn);
+    k_ccl_flatten<<<blocks, 256, 0, st>>>(parent, g.N);
+    k_ccl_count<<<nb, 1024, 0, st>>>(parent, rank, block_tot, g.N);
+    k_scan_blocks<<<1, 1024, 0, st>>>(block_tot, block_off, nb, n_out);
+    k_ccl_relabel<<<blocks, 256, 0, st>>>(parent, rank, block_off, label, root_of, root_cap, g.N);
+    if (launches) *launches += 6;
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Step 3: distinct tag pairs of opposite occupied cells around near-contact
+// cells, deduplicated in an open-addressing set of 64-bit keys
+// (field << 60 | lo << 30 | hi).
+
+__device__ __forceinline__ unsigned long long pair_key(int f, int lo, int hi) {
+    return ((unsigned long long)f << 60) | ((unsigned long long)lo << 30) | (unsigned long long)hi;
+}
+
+__device__ __forceinline__ void set_insert(unsigned long long* table, int mask, unsigned long long key,
+                                           int* overflow) {
+    unsigned long long h = key * 0x9E3779B97F4A7C15ull;
+    int s = (int)(h >> 40) & mask;
+    for (int p = 0; p <= mask; ++p) {
+        unsigned long long old = atomicCAS(table + s, kEmptyKey, key);
+        if (old == kEmptyKey || old == key) return;
+        s = (s + 1) & mask;
+    }
+    atomicExch(overflow, 1);
+}
+
+__global__ void k_pairs(const uint32_t* __restrict__ ncmap_f, const uint32_t* __restrict__ bits_f,
+                        const int* __restrict__ label_f, Dims g, int w, int f,
+                        unsigned long long* table, int mask, int* overflow) {
+    long long words = (long long)g.rows * g.W;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words;
+         idx += (long long)gridDim.x * blockDim.x) {
+        uint32_t m = ncmap_f[idx];
+        if (!m) continue;
+        int row = (int)(idx / g.W), wi = (int)(idx - (long long)row * g.W);
+        int j = row % g.ny, k = row / g.ny;
+        while (m) {
+            int b = __ffs(m) - 1;
+            m &= m - 1u;
+            int i = wi * 32 + b;
+            for (int dz = 0; dz <= w; ++dz)
+                for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy)
+                    for (int dx = ((dz == 0 && dy == 0) ? 1 : -w); dx <= w; ++dx) {
+                        int ia = wrapi(i + dx, g.nx), ja = wrapi(j + dy, g.ny), ka = wrapi(k + dz, g.nz);
+                        int ib = wrapi(i - dx, g.nx), jb = wrapi(j - dy, g.ny), kb = wrapi(k - dz, g.nz);
+                        if (!bit_at(bits_f, g.W, ka * g.ny + ja, ia)) continue;
+                        if (!bit_at(bits_f, g.W, kb * g.ny + jb, ib)) continue;
+                        int la = label_f[cell(ia, ja, ka, g)], lb = label_f[cell(ib, jb, kb, g)];
+                        if (la == lb) continue;
+                        set_insert(table, mask, pair_key(f, la < lb ? la : lb, la < lb ? lb : la), overflow);
+                    }
+        }
+    }
+}
+
+__global__ void k_compact_set(const unsigned long long* __restrict__ table, int cap,
+                              unsigned long long* __restrict__ out, unsigned long long* count) {
+    for (int base = blockIdx.x * blockDim.x; base < cap; base += gridDim.x * blockDim.x) {
+        int s = base + threadIdx.x;
+        unsigned long long key = s < cap ? table[s] : kEmptyKey;
+        long long slot = warp_append(key != kEmptyKey, count);
+        if (slot >= 0) out[slot] = key;
+    }
+}
+
+cudaError_t tag_pairs(const uint32_t* ncmap_f, const uint32_t* bits_f, const int* label_f, const Dims& g,
+                      int w, int f, unsigned long long* table, int cap, int* overflow, cudaStream_t st) {
+    long long words = (long long)g.rows * g.W;
+    k_pairs<<<grid_for(words, 128), 128, 0, st>>>(ncmap_f, bits_f, label_f, g, w, f, table, cap - 1, overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t compact_pairs(const unsigned long long* table, int cap, unsigned long long* out,
+                          unsigned long long* count, cudaStream_t st) {
+    k_compact_set<<<grid_for(cap, 256), 256, 0, st>>>(table, cap, out, count);
+    return cudaGetLastError();
+}
+
+}  // namespace vof
