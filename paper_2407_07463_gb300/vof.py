@@ -57,7 +57,7 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_pair_stats", "vof_plic_volume", "vof_plic_alpha", "vof_normals",
            "vof_state_size", "vof_get_state", "vof_set_state", "vof_launch_count",
            "vof_status_string", "vof_destroy", "vof_profile_enable", "vof_profile_read",
-           "vof_profile_class_name"]
+           "vof_profile_class_name", "vof_label_noalloc"]
 
 
 def lib():
@@ -94,6 +94,7 @@ def lib():
         "vof_profile_enable": (C.c_int, [vp, i32]),
         "vof_profile_read": (C.c_int, [vp, vp, vp, i32]),
         "vof_profile_class_name": (C.c_char_p, [i32]),
+        "vof_label_noalloc": (C.c_int, [vp, i32, i32, i32, i32, dbl, i32, vp, C.POINTER(i32), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -169,6 +170,19 @@ def vof_pair_stats(cen, box, n_rbins, dr, n_tbins=150, dtheta=np.pi / 150, tie_t
                                 _ptr(hist_r), _ptr(hist_rt), _ptr(moments), _stream(stream)),
            "vof_pair_stats")
     return hist_r, hist_rt, moments
+
+
+def vof_label_noalloc(c, precision=VOF_FP64, tag_tau=0.0, connectivity=6, out=None, stream=None):
+    """Tags of one field c[nz][ny][nx] (device tensor) through the entry point
+    that allocates nothing inside the library; returns (labels, n)."""
+    import torch
+    nz, ny, nx = c.shape
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.int32, device=c.device)
+    n = C.c_int32()
+    _check(lib().vof_label_noalloc(_ptr(c), precision, nx, ny, nz, float(tag_tau), connectivity,
+                                   _ptr(out), C.byref(n), _stream(stream)), "vof_label_noalloc")
+    return out, n.value
 
 
 # --------------------------------------------------------------------------- context
