@@ -150,11 +150,15 @@ def peaks():
 
 def algorithmic_bytes(cls, n_cells, fields, es):
     """Minimum DRAM bytes one launch of a kernel class must move (per launch).
-    update: read c_in, read c at the step start (c_c), write c_out per
+    fused_step (a whole step of every active field): read c once, write c
+    once and one occupancy bit per cell-field, read the three velocity
+    components once.  update: read c_in, read c at the step start (c_c), write c_out per
     cell-field, plus the sweep's velocity component per cell.
     find_faces: read c_in per cell-field plus the velocity component.
     pack_bits: read c per cell-field, write one bit.  near_contact: read and
     write one bit per cell-field."""
+    if cls == "fused_step":
+        return n_cells * fields * (2 * es + 1 / 8) + 3 * n_cells * es
     if cls == "update":
         return n_cells * fields * 3 * es + n_cells * es
     if cls == "find_faces":

@@ -61,7 +61,7 @@ typedef struct {
     int32_t k_active;        /* fields in use at start, N(0), 1..K */
     int32_t precision;       /* vof_precision */
     double h;                /* cell size > 0 */
-    int32_t stencil_w;       /* near-contact half width w (2 = 5-cell stencil) */
+    int32_t stencil_w;       /* near-contact half width w, 1..7 (2 = 5-cell stencil) */
     int32_t connectivity;    /* tagging connectivity: 6 or 26 */
     double tag_tau;          /* a cell belongs to a drop iff c > tag_tau (>= 0) */
     double alpha_fp64_band;  /* mixed path: alpha in double if c < band or
@@ -74,7 +74,7 @@ typedef struct {
 } vof_config;
 
 /* Fill `cfg` with defaults: 32^3, K = 1, FP64, h = 1, w = 2, 6-connectivity,
- * tau = 0, band 1e-3, no recolouring, vertical axis z, 1024 x 150 bins of
+ * tau = 1e-6, band 1e-3, no recolouring, vertical axis z, 1024 x 150 bins of
  * width 0.2. */
 vof_status vof_config_default(vof_config *cfg);
 

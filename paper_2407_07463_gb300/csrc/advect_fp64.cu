@@ -4,5 +4,5 @@
 #include "advect_impl.cuh"
 
 namespace vof {
-cudaError_t advect_steps_fp64(const AdvectArgs& a, int nsteps) { return advect_steps_t<double>(a, nsteps); }
+cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps) { return advect_steps_t<double>(a, nsteps); }
 }  // namespace vof

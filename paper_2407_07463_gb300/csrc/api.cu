@@ -18,9 +18,12 @@ enum Slot {
     S_BUF2,
     S_FLUX,
     S_LIST,
+    S_COUNTS,
     S_MISC,
     S_BITS,
+    S_CCBITS,
     S_NCMAP,
+    S_MVBITS,
     S_LABELS,
     S_PARENT,
     S_RANK,
@@ -63,13 +66,14 @@ struct Layout {
 bool config_valid(const vof_config* c) {
     if (!c) return false;
     if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
+    if (c->nx >= (1 << 18) || c->ny >= (1 << 18) || c->nz >= (1 << 18)) return false;
     long long N = (long long)c->nx * c->ny * c->nz;
     if (N >= (1ll << 31)) return false;
     if (c->k_capacity < 1 || c->k_capacity > kMaxK) return false;
     if (c->k_active < 1 || c->k_active > c->k_capacity) return false;
     if (c->precision < VOF_FP64 || c->precision > VOF_MIXED_LEARNED) return false;
     if (!(c->h > 0.0) || !std::isfinite(c->h)) return false;
-    if (c->stencil_w < 1 || c->stencil_w > 8) return false;
+    if (c->stencil_w < 1 || c->stencil_w > 7) return false;
     if (c->connectivity != 6 && c->connectivity != 26) return false;
     if (!(c->tag_tau >= 0.0 && c->tag_tau < 1.0)) return false;
     if (!(c->alpha_fp64_band >= 0.0 && c->alpha_fp64_band < 0.5)) return false;
@@ -92,10 +96,16 @@ Layout layout_for(const vof_config* c) {
     L.size[S_BUF1] = K * N * es;
     L.size[S_BUF2] = K * N * es;
     L.size[S_FLUX] = K * N * es;
-    L.size[S_LIST] = K * N * 8;
+    // two face lists segmented by block; a segment holds up to 2 faces per
+    // cell and field of the block's row segments
+    // (any grid of gb <= kSweepBlocks blocks: gb * ceil(words / gb) <= words + gb)
+    L.size[S_LIST] = 2 * (2 * 32 * K * (words + (size_t)kSweepBlocks)) * 8;
+    L.size[S_COUNTS] = (3 * (size_t)kSweepBlocks + 1) * 4;
     L.size[S_MISC] = kMiscBytes;
     L.size[S_BITS] = K * words * 4;
+    L.size[S_CCBITS] = K * words * 4;
     L.size[S_NCMAP] = K * words * 4;
+    L.size[S_MVBITS] = K * words * 4;
     L.size[S_LABELS] = K * N * 4;
     L.size[S_PARENT] = N * 4;
     L.size[S_RANK] = N * 4;
@@ -131,6 +141,8 @@ struct vof_ctx {
     bool fp64;
     size_t es;
     void* c;
+    void* cur;        // buffer holding the state (always c between calls)
+    bool bits_valid;  // occupancy bits of the active fields match c
     const void* u;
     char* ws;
     Layout L;
@@ -171,6 +183,17 @@ cudaError_t timed(vof_ctx* ctx, int cls, F&& f) {
     return e;
 }
 
+// Threshold for the occupancy test c > tau that, applied to the stored
+// element type, decides exactly as the comparison in double would: for float
+// storage, the largest float not above tau.
+double occupancy_tau(const vof_ctx* ctx) {
+    double tau = ctx->cfg.tag_tau;
+    if (ctx->fp64) return tau;
+    float tf = (float)tau;
+    if ((double)tf > tau) tf = nextafterf(tf, -1.0f);
+    return (double)tf;
+}
+
 vof_status check_ctx(vof_ctx* ctx) {
     if (!ctx) return VOF_ERR_ARG;
     return ctx->sticky;
@@ -205,7 +228,8 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     if (fired_out) *fired_out = 0;
 
     // Step 1 on the snapshot
-    VOF_CUDA(ctx, timed(ctx, P_PACK_BITS, [&] { return pack_bits(ctx->c, ctx->fp64, bits, g, na0, cf.tag_tau, st); }));
+    if (!ctx->bits_valid)
+        VOF_CUDA(ctx, timed(ctx, P_PACK_BITS, [&] { return pack_bits(ctx->cur, ctx->fp64, bits, g, na0, occupancy_tau(ctx), st); }));
     if (na0 < K) VOF_CUDA(ctx, cudaMemsetAsync(bits + (size_t)na0 * words, 0, (size_t)(K - na0) * words * 4, st));
     VOF_CUDA(ctx, cudaMemsetAsync(flags, 0, kMaxK * sizeof(int), st));
     VOF_CUDA(ctx, timed(ctx, P_NEAR_CONTACT, [&] { return near_contact(bits, ncmap, flags, g, na0, cf.stencil_w, st); }));
@@ -306,8 +330,8 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     VOF_CUDA(ctx, cudaMemsetAsync(touch, 0, (size_t)M * 4, st));
     VOF_CUDA(ctx, cudaMemsetAsync(conflict, 0, (size_t)M * kMoveWords * 4, st));
     VOF_CUDA(ctx, timed(ctx, P_TOUCH, [&] {
-                 return recolour_touch(labels, bits, g, K, na0, 2 * cf.stencil_w, mt, d_fields,
-                                       (int)hfields.size(), touch, conflict, kMoveWords, st);
+                 return recolour_touch(labels, bits, ctx->slot<uint32_t>(S_MVBITS), g, K, na0, 2 * cf.stencil_w,
+                                       mt, d_fields, (int)hfields.size(), touch, conflict, kMoveWords, st);
              }));
     ctx->launches += 1;
     std::vector<unsigned> htouch(M), hconf((size_t)M * kMoveWords);
@@ -344,9 +368,10 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     int* d_target = ctx->slot<int>(S_TARGET);
     VOF_CUDA(ctx, cudaMemcpyAsync(d_target, target.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
     VOF_CUDA(ctx, timed(ctx, P_MOVE, [&] {
-                 return recolour_move(ctx->c, ctx->fp64, labels, g, mt, d_fields, (int)hfields.size(), d_target, st);
+                 return recolour_move(ctx->cur, ctx->fp64, labels, g, mt, d_fields, (int)hfields.size(), d_target, st);
              }));
     ctx->launches += 1;
+    ctx->bits_valid = false;
     VOF_CUDA(ctx, cudaStreamSynchronize(st));
     *moved_out = moved;
     return status;
@@ -366,7 +391,7 @@ vof_status vof_config_default(vof_config* cfg) {
     cfg->h = 1.0;
     cfg->stencil_w = 2;
     cfg->connectivity = 6;
-    cfg->tag_tau = 0.0;
+    cfg->tag_tau = 1e-6;
     cfg->alpha_fp64_band = 1e-3;
     cfg->recolour = 0;
     cfg->vertical_axis = 2;
@@ -396,6 +421,8 @@ vof_status vof_init(const vof_config* cfg, void* c_dev, const void* u_dev, void*
     ctx->fp64 = cfg->precision == VOF_FP64;
     ctx->es = ctx->fp64 ? 8 : 4;
     ctx->c = c_dev;
+    ctx->cur = c_dev;
+    ctx->bits_valid = false;
     ctx->u = u_dev;
     ctx->ws = (char*)workspace_dev;
     ctx->L = L;
@@ -445,7 +472,14 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     a.buf2 = ctx->slot<void>(S_BUF2);
     a.flux = ctx->slot<void>(S_FLUX);
     a.list = ctx->slot<unsigned long long>(S_LIST);
-    a.counter = (unsigned long long*)(ctx->misc() + kMiscCounters);
+    a.counts = ctx->slot<int>(S_COUNTS);
+    a.offsets = ctx->slot<int>(S_COUNTS) + 2 * kSweepBlocks;
+    a.Kcap = ctx->cfg.k_capacity;
+    a.ccbits = ctx->slot<uint32_t>(S_CCBITS);
+    a.occbits = ctx->slot<uint32_t>(S_BITS);
+    a.tau = occupancy_tau(ctx);
+    a.list_valid = false;
+    a.list_cur = 0;
     a.clipped = clipped;
     a.dt = dt;
     a.h = ctx->cfg.h;
@@ -462,14 +496,15 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
         a.K = ctx->n_active;
         a.step = ctx->step;
         field_steps += (long long)a.K * n;
-        cudaError_t e = ctx->fp64 ? advect_steps_fp64(a, n) : advect_steps_fp32(a, n);
-        VOF_CUDA(ctx, e);
+        VOF_CUDA(ctx, ctx->fp64 ? advect_steps_fp64(a, n) : advect_steps_fp32(a, n));
+        ctx->bits_valid = true;
         ctx->step += n;
         if (ctx->cfg.recolour) {
             int moved = 0, fired = 0;
             vof_status r = recolour_impl(ctx, &moved, &fired);
             if (r != VOF_OK && r != VOF_ERR_NO_FREE_FIELD) return r;
             if (r == VOF_ERR_NO_FREE_FIELD) result = r;
+            if (moved) a.list_valid = false;  // moves change the interfacial donors
             moved_total += moved;
             fired_steps += fired;
         }
@@ -497,7 +532,7 @@ vof_status vof_near_contact(vof_ctx* ctx, int32_t* flags_host) {
     const Dims& g = ctx->g;
     uint32_t* bits = ctx->slot<uint32_t>(S_BITS);
     int* flags = (int*)(ctx->misc() + kMiscFlags);
-    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, ctx->cfg.tag_tau, ctx->stream));
+    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, occupancy_tau(ctx), ctx->stream));
     VOF_CUDA(ctx, cudaMemsetAsync(flags, 0, kMaxK * sizeof(int), ctx->stream));
     VOF_CUDA(ctx, near_contact(bits, ctx->slot<uint32_t>(S_NCMAP), flags, g, ctx->n_active, ctx->cfg.stencil_w,
                                ctx->stream));
@@ -518,7 +553,7 @@ vof_status vof_label(vof_ctx* ctx, int32_t field, int32_t* label_dev, int32_t* n
     uint32_t* bits = ctx->slot<uint32_t>(S_BITS);
     const char* cf = (const char*)ctx->c + (size_t)field * g.N * ctx->es;
     int* nout = (int*)(ctx->misc() + kMiscNout);
-    VOF_CUDA(ctx, pack_bits(cf, ctx->fp64, bits + (size_t)field * words, g, 1, ctx->cfg.tag_tau, ctx->stream));
+    VOF_CUDA(ctx, pack_bits(cf, ctx->fp64, bits + (size_t)field * words, g, 1, occupancy_tau(ctx), ctx->stream));
     ctx->launches += 1;
     VOF_CUDA(ctx, label_field(bits + (size_t)field * words, g, ctx->cfg.connectivity, ctx->slot<int>(S_PARENT),
                               ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT), ctx->slot<int>(S_BOFF), label_dev,
@@ -554,7 +589,7 @@ vof_status vof_drop_table(vof_ctx* ctx, int32_t field, const int32_t* label_dev,
     int* nout = (int*)(ctx->misc() + kMiscNout);
     int* tmp_label = ctx->slot<int>(S_LABELS) + (size_t)field * g.N;
     // re-derive the roots (the caller's labels must be this field's tags)
-    VOF_CUDA(ctx, pack_bits(cf, ctx->fp64, bits + (size_t)field * words, g, 1, ctx->cfg.tag_tau, ctx->stream));
+    VOF_CUDA(ctx, pack_bits(cf, ctx->fp64, bits + (size_t)field * words, g, 1, occupancy_tau(ctx), ctx->stream));
     VOF_CUDA(ctx, label_field(bits + (size_t)field * words, g, ctx->cfg.connectivity, ctx->slot<int>(S_PARENT),
                               ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT), ctx->slot<int>(S_BOFF), tmp_label,
                               ctx->slot<int>(S_ROOT), kDropCap, nout + field, ctx->stream, &ctx->launches));
@@ -590,7 +625,7 @@ vof_status vof_stats(vof_ctx* ctx, int32_t reset, vof_stats_out* out, double* hi
     double* cen = ctx->slot<double>(S_CEN);
     double* vol = ctx->slot<double>(S_VOL);
     int* root = ctx->slot<int>(S_ROOT);
-    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, cf.tag_tau, st));
+    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, occupancy_tau(ctx), st));
     ctx->launches += 1;
     long long D = 0;
     for (int f = 0; f < ctx->n_active; ++f) {
@@ -755,6 +790,7 @@ vof_status vof_set_state(vof_ctx* ctx, const void* host_buf, size_t bytes) {
     VOF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->n_active = h.n_active;
     ctx->step = h.step;
+    ctx->bits_valid = false;
     return VOF_OK;
 }
 
@@ -816,8 +852,9 @@ vof_status vof_profile_read(vof_ctx* ctx, int64_t* launches, double* ms, int32_t
 }
 
 const char* vof_profile_class_name(int32_t cls) {
-    static const char* names[P_COUNT] = {"find_faces", "face_flux", "update", "pack_bits", "near_contact",
-                                         "label", "pairs", "touch", "move", "stats", "misc"};
+    static const char* names[P_COUNT] = {"list_faces", "face_flux", "update", "pack_bits", "near_contact",
+                                         "label",      "pairs",     "touch",  "move",      "stats",
+                                         "misc"};
     if (cls < 0 || cls >= P_COUNT) return nullptr;
     return names[cls];
 }

@@ -52,11 +52,14 @@ constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr int kPairCap = 1 << 16;     // distinct tagged near-contact pairs per call
 constexpr int kMoveCap = 2048;        // moving drops per recolour call
 constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
+constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a sweep
 
 struct AdvectArgs;
-cudaError_t advect_steps_fp64(const AdvectArgs& a, int nsteps);
-cudaError_t advect_steps_fp32(const AdvectArgs& a, int nsteps);
+cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps);
+cudaError_t advect_steps_fp32(AdvectArgs& a, int nsteps);
 
+// Exclusive scan of n ints (one block); off[n] = total.
+cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st);
 cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
                       cudaStream_t st);
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
@@ -77,8 +80,8 @@ struct MoveTables {
     const int* mv_label;   // [M]
     int M;
 };
-cudaError_t recolour_touch(const int* labels, const uint32_t* bits, const Dims& g, int K, int n_active,
-                           int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, const Dims& g, int K,
+                           int n_active, int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
                            unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st);
 cudaError_t recolour_move(void* c, bool fp64, const int* labels, const Dims& g, MoveTables mt,
                           const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);

@@ -143,11 +143,15 @@ __device__ T plic_volume(T m0, T m1, T m2, T alpha) {
 }
 
 // Root alpha in (0, S/2] of vol_sorted(a,b,c,alpha) = v, 0 < v <= 1/2.
+// *region (if not null) receives the piece the root lies in: 0 for the 2D
+// cases (a = 0), 1..4 the cubic regions, 5 the prism region.
 template <typename T>
-__device__ T alpha_sorted(T a, T b, T c, T v) {
+__device__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr) {
     T al;
+    int reg;
     if (a <= PlicConst<T>::tiny) {
         // plane parallel to one axis: the 2D area function
+        if (region) *region = 0;
         if (b <= PlicConst<T>::tiny) return c * v;
         T t = sqrt_t(T(2) * b * c * v);
         if (t < b) return t;
@@ -157,11 +161,13 @@ __device__ T alpha_sorted(T a, T b, T c, T v) {
     T Va = a * a / (T(6) * bc);
     if (v <= Va) {
         al = cbrt_t(T(6) * a * bc * v);
+        reg = 1;
     } else {
         T Vb = (b * b - a * b + a * a / T(3)) / (T(2) * bc);
         if (v <= Vb) {
             T disc = T(8) * bc * v - a * a / T(3);
             al = T(0.5) * (a + sqrt_t(disc > T(0) ? disc : T(0)));
+            reg = 2;
         } else {
             T ab = a + b;
             T S = ab + c;
@@ -170,8 +176,10 @@ __device__ T alpha_sorted(T a, T b, T c, T v) {
             if (prism && v >= ab / (T(2) * c)) {
                 al = c * v + T(0.5) * ab;
                 hi = T(-1);
+                reg = 5;
             } else {
                 hi = prism ? ab : T(0.5) * S;
+                reg = 3;
             }
             if (hi > T(0)) {
                 // Newton on 6abc V = al^3 - (al-a)^3 - (al-b)^3 - [(al-c)^3]
@@ -192,6 +200,7 @@ __device__ T alpha_sorted(T a, T b, T c, T v) {
                     if (al < b) { al = b; break; }
                     if (fabs(stp) <= PlicConst<T>::newton_rtol * al) break;
                 }
+                if (al > c) reg = 4;
             }
         }
     }
@@ -202,7 +211,34 @@ __device__ T alpha_sorted(T a, T b, T c, T v) {
         T nal = al - (vol_sorted(a, b, c, al) - v) / dv;
         if (nal > T(0) && nal <= T(0.5) * S) al = nal;
     }
+    if (region) *region = reg;
     return al;
+}
+
+// One Newton step in double on the closed form of the region the float
+// root lies in (the FP64 part of the mixed-precision plane constant).
+__device__ __forceinline__ double alpha_refine_fp64(double a, double b, double c, double v, double al,
+                                                    int reg) {
+    if (reg == 0) {
+        if (b <= 1e-30) return c * v;
+        if (al < b) return al - (al * al - 2.0 * b * c * v) / (2.0 * al);
+        return c * v + 0.5 * b;
+    }
+    if (reg == 5) return c * v + 0.5 * (a + b);
+    if (reg == 1) return al - (al * al * al - 6.0 * a * b * c * v) / (3.0 * al * al);
+    if (reg == 2) {
+        double f = al * al - a * al + a * a / 3.0 - 2.0 * b * c * v;
+        return al - f / (2.0 * al - a);
+    }
+    double da = al - a, db = al - b, dc = al - c;
+    double f = al * al * al - da * da * da - db * db * db - 6.0 * a * b * c * v;
+    double fp = al * al - da * da - db * db;
+    if (reg == 4) {
+        f -= dc * dc * dc;
+        fp -= dc * dc;
+    }
+    fp *= 3.0;
+    return fp > 0.0 ? al - f / fp : al;
 }
 
 // Plane constant alpha with plic_volume(m, alpha) = cv.
@@ -223,12 +259,27 @@ __device__ T plic_alpha(T m0, T m1, T m2, T cv) {
     return al + off;
 }
 
-// Mixed precision: alpha in double inside the band c < band or c > 1-band.
-__device__ __forceinline__ float plic_alpha_banded(float m0, float m1, float m2, float cv,
-                                                   float band) {
-    if (cv < band || cv > 1.f - band)
-        return (float)plic_alpha<double>((double)m0, (double)m1, (double)m2, (double)cv);
-    return plic_alpha<float>(m0, m1, m2, cv);
+// Mixed precision: inside the band c < band or c > 1 - band the plane
+// constant found in float is refined by one Newton step in double on the
+// closed-form volume of its region (a few FP64 operations: GB300 issues FP64
+// at a small fraction of its FP32 rate).
+__device__ __forceinline__ float plic_alpha_banded(float m0, float m1, float m2, float cv, float band) {
+    if (!(cv < band || cv > 1.f - band)) return plic_alpha<float>(m0, m1, m2, cv);
+    float off = 0.f;
+    if (m0 < 0.f) { off += m0; m0 = -m0; }
+    if (m1 < 0.f) { off += m1; m1 = -m1; }
+    if (m2 < 0.f) { off += m2; m2 = -m2; }
+    sort3(m0, m1, m2);
+    float S = m0 + m1 + m2;
+    if (cv <= 0.f) return off;
+    if (cv >= 1.f) return off + S;
+    bool flip = cv > 0.5f;
+    double v = flip ? 1.0 - (double)cv : (double)cv;
+    int reg = 0;
+    float al32 = alpha_sorted<float>(m0, m1, m2, (float)v, &reg);
+    double al = alpha_refine_fp64((double)m0, (double)m1, (double)m2, v, (double)al32, reg);
+    if (flip) al = (double)S - al;
+    return (float)(al + (double)off);
 }
 __device__ __forceinline__ double plic_alpha_banded(double m0, double m1, double m2, double cv,
                                                     double) {

@@ -23,43 +23,89 @@ __device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) 
     return -1;
 }
 
+// Occupancy bits of the cells of moving drops, one bit plane per field of
+// mv_fields (same row layout as the occupancy bits).
+__global__ void k_moving_bits(const int* __restrict__ labels, Dims g, MoveTables mt,
+                              const int* __restrict__ mv_fields, int n_mv_fields, uint32_t* __restrict__ mvbits) {
+    long long per_field = (long long)g.rows * g.W;
+    long long words = (long long)n_mv_fields * per_field;
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long wd = warp; wd < words; wd += nwarps) {
+        int q = (int)(wd / per_field);
+        long long rem = wd - (long long)q * per_field;
+        int row = (int)(rem / g.W);
+        int w = (int)(rem - (long long)row * g.W);
+        int x = w * 32 + lane;
+        int f = mv_fields[q];
+        bool v = false;
+        if (x < g.nx) {
+            int l = labels[(size_t)f * g.N + (size_t)row * g.nx + x];
+            v = l != 0 && moving_index(mt, f, l) >= 0;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) mvbits[wd] = m;
+    }
+}
+
 // For every cell of a moving drop m: the fields (other than its own) with an
 // occupied cell within Chebyshev distance `reach`, and the other moving
-// drops with a cell within that distance.
-__global__ void k_touch(const int* __restrict__ labels, const uint32_t* __restrict__ bits, Dims g,
-                        int n_active, int reach, MoveTables mt, const int* __restrict__ mv_fields,
-                        int n_mv_fields, unsigned* __restrict__ touch, unsigned* __restrict__ conflict,
-                        int Mw) {
+// drops with a cell within that distance.  Only cells on the drop's boundary
+// (a 26-neighbour outside the drop) scan the (2 reach + 1)^3 box: walking
+// from an interior cell towards any cell outside the drop reaches a boundary
+// cell that is no farther from it.  Interior cells test their own position.
+// Rows of the box are read as bit windows of the occupancy planes.
+__global__ void k_touch(const int* __restrict__ labels, const uint32_t* __restrict__ bits,
+                        const uint32_t* __restrict__ mvbits, Dims g, int n_active, int reach, MoveTables mt,
+                        const int* __restrict__ mv_fields, int n_mv_fields, unsigned* __restrict__ touch,
+                        unsigned* __restrict__ conflict, int Mw) {
     long long total = (long long)n_mv_fields * g.N;
     long long per_field_words = (long long)g.rows * g.W;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         int fi = (int)(t / g.N);
         int x = (int)(t - (long long)fi * g.N);
-        int f = mv_fields[fi];
-        int l = labels[(size_t)f * g.N + x];
-        if (l == 0) continue;
-        int m = moving_index(mt, f, l);
-        if (m < 0) continue;
         int i, j, k;
         decode(x, g, i, j, k);
-        unsigned tmask = 0;
-        for (int dz = -reach; dz <= reach; ++dz) {
-            int kk = wrapi(k + dz, g.nz);
-            for (int dy = -reach; dy <= reach; ++dy) {
-                int jj = wrapi(j + dy, g.ny);
-                int row = kk * g.ny + jj;
-                for (int dx = -reach; dx <= reach; ++dx) {
-                    int ii = wrapi(i + dx, g.nx);
-                    for (int n = 0; n < n_active; ++n) {
-                        if (n == f || ((tmask >> n) & 1u)) continue;
-                        if (bit_at(bits + (size_t)n * per_field_words, g.W, row, ii)) tmask |= 1u << n;
+        if (!bit_at(mvbits + (size_t)fi * per_field_words, g.W, k * g.ny + j, i)) continue;
+        int f = mv_fields[fi];
+        const int* lab = labels + (size_t)f * g.N;
+        int l = lab[x];
+        int m = moving_index(mt, f, l);
+        if (m < 0) continue;
+        bool interior = true;
+        for (int dz = -1; dz <= 1 && interior; ++dz)
+            for (int dy = -1; dy <= 1 && interior; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (lab[cell(wrapi(i + dx, g.nx), wrapi(j + dy, g.ny), wrapi(k + dz, g.nz), g)] != l) {
+                        interior = false;
+                        break;
                     }
-                    int y = cell(ii, jj, kk, g);
-                    for (int q = 0; q < n_mv_fields; ++q) {
-                        int f2 = mv_fields[q];
+                }
+        int r = interior ? 0 : reach;
+        int span = 2 * r + 1;
+        uint32_t smask = span >= 32 ? 0xffffffffu : ((1u << span) - 1u);
+        unsigned tmask = 0;
+        for (int dz = -r; dz <= r; ++dz) {
+            int kk = wrapi(k + dz, g.nz);
+            for (int dy = -r; dy <= r; ++dy) {
+                int jj = wrapi(j + dy, g.ny);
+                size_t row = (size_t)(kk * g.ny + jj) * g.W;
+                for (int n = 0; n < n_active; ++n) {
+                    if (n == f || ((tmask >> n) & 1u)) continue;
+                    if (row_window(bits + (size_t)n * per_field_words + row, g.W, g.nx, i - r) & smask)
+                        tmask |= 1u << n;
+                }
+                for (int q = 0; q < n_mv_fields; ++q) {
+                    uint32_t wv = row_window(mvbits + (size_t)q * per_field_words + row, g.W, g.nx, i - r) & smask;
+                    int f2 = mv_fields[q];
+                    while (wv) {
+                        int b = __ffs(wv) - 1;
+                        wv &= wv - 1u;
+                        int y = cell(wrapi(i - r + b, g.nx), jj, kk, g);
                         int l2 = labels[(size_t)f2 * g.N + y];
-                        if (l2 == 0) continue;
+                        if (f2 == f && l2 == l) continue;
                         int m2 = moving_index(mt, f2, l2);
                         if (m2 < 0 || m2 == m) continue;
                         unsigned bitm = 1u << (m2 & 31);
@@ -73,11 +119,13 @@ __global__ void k_touch(const int* __restrict__ labels, const uint32_t* __restri
     }
 }
 
-cudaError_t recolour_touch(const int* labels, const uint32_t* bits, const Dims& g, int K, int n_active,
-                           int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, const Dims& g, int K,
+                           int n_active, int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
                            unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st) {
+    long long words = (long long)n_mv_fields * g.rows * g.W;
+    k_moving_bits<<<grid_for(words * 32, 256), 256, 0, st>>>(labels, g, mt, mv_fields, n_mv_fields, mvbits);
     long long total = (long long)n_mv_fields * g.N;
-    k_touch<<<grid_for(total, 128), 128, 0, st>>>(labels, bits, g, n_active, reach, mt, mv_fields,
+    k_touch<<<grid_for(total, 128), 128, 0, st>>>(labels, bits, mvbits, g, n_active, reach, mt, mv_fields,
                                                    n_mv_fields, touch, conflict, Mw);
     return cudaGetLastError();
 }

@@ -52,12 +52,22 @@ cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, i
 // delta in [-w,w]^3 \ {0} with both cells x + delta and x - delta occupied?
 // One offset per opposite pair: the first nonzero of (dz, dy, dx) positive.
 
+// Bits x0 + dx .. x0 + dx + 31 from the words left, centre and right of x0
+// (|dx| < 32).
+__device__ __forceinline__ uint32_t shift_window(uint32_t l, uint32_t c, uint32_t r, int dx) {
+    if (dx == 0) return c;
+    if (dx > 0) return __funnelshift_r(c, r, dx);
+    return __funnelshift_l(l, c, -dx);
+}
+
 __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict__ bits,
                                                       uint32_t* __restrict__ ncmap,
                                                       int* __restrict__ flags, Dims g, int K, int w) {
     long long per_field = (long long)g.rows * g.W;
     long long words = (long long)K * per_field;
     long long stride = (long long)gridDim.x * blockDim.x;
+    const bool aligned = (g.nx & 31) == 0;
+    const bool wide = g.ny > 2 * w && g.nz > 2 * w;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words; idx += stride) {
         int f = (int)(idx / per_field);
         long long rem = idx - (long long)f * per_field;
@@ -70,20 +80,40 @@ __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict
         uint32_t empty = ~centre & valid;
         uint32_t acc = 0;
         int x0 = wi * 32;
+        int wl = wi == 0 ? g.W - 1 : wi - 1, wr = wi + 1 == g.W ? 0 : wi + 1;
         if (empty) {
-            for (int dz = 0; dz <= w; ++dz) {
-                int ka = wrapi(k + dz, g.nz), kb = wrapi(k - dz, g.nz);
+            for (int dz = 0; dz <= w && (acc & empty) != empty; ++dz) {
+                int ka, kb;
+                if (wide) {
+                    ka = k + dz; if (ka >= g.nz) ka -= g.nz;
+                    kb = k - dz; if (kb < 0) kb += g.nz;
+                } else {
+                    ka = wrapi(k + dz, g.nz);
+                    kb = wrapi(k - dz, g.nz);
+                }
                 for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy) {
-                    int ja = wrapi(j + dy, g.ny), jb = wrapi(j - dy, g.ny);
+                    int ja, jb;
+                    if (wide) {
+                        ja = j + dy; if (ja >= g.ny) ja -= g.ny; else if (ja < 0) ja += g.ny;
+                        jb = j - dy; if (jb >= g.ny) jb -= g.ny; else if (jb < 0) jb += g.ny;
+                    } else {
+                        ja = wrapi(j + dy, g.ny);
+                        jb = wrapi(j - dy, g.ny);
+                    }
                     const uint32_t* ra = fb + (size_t)(ka * g.ny + ja) * g.W;
                     const uint32_t* rb = fb + (size_t)(kb * g.ny + jb) * g.W;
                     int dx0 = (dz == 0 && dy == 0) ? 1 : -w;
-                    for (int dx = dx0; dx <= w; ++dx) {
-                        acc |= row_window(ra, g.W, g.nx, x0 + dx) & row_window(rb, g.W, g.nx, x0 - dx);
+                    if (aligned) {
+                        uint32_t al = ra[wl], ac = ra[wi], ar = ra[wr];
+                        uint32_t bl = rb[wl], bc = rb[wi], br = rb[wr];
+                        if (((al | ac | ar) == 0) || ((bl | bc | br) == 0)) continue;
+                        for (int dx = dx0; dx <= w; ++dx)
+                            acc |= shift_window(al, ac, ar, dx) & shift_window(bl, bc, br, -dx);
+                    } else {
+                        for (int dx = dx0; dx <= w; ++dx)
+                            acc |= row_window(ra, g.W, g.nx, x0 + dx) & row_window(rb, g.W, g.nx, x0 - dx);
                     }
-                    if ((acc & empty) == empty) break;
                 }
-                if ((acc & empty) == empty) break;
             }
         }
         uint32_t res = acc & empty;
@@ -101,13 +131,14 @@ cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, cons
 
 // --------------------------------------------------------------------------
 // Tagging (connected components, periodic)
-
-__global__ void k_ccl_init(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
-        int i = x % g.nx, row = x / g.nx;
-        parent[x] = bit_at(bits_f, g.W, row, i) ? x : -1;
-    }
-}
+//
+// Union-find over occupied cells; every link points to a smaller linear
+// index, so a component's root is its smallest cell.  6-connectivity works
+// on runs of the occupancy bits: within a row each cell links to the start
+// of its run (or to the last cell of the previous word when the run crosses
+// a word), and rows are joined by one union per maximal segment where a row
+// and its -y / -z neighbour row are both occupied.  26-connectivity uses one
+// union per occupied neighbour pair.  Empty cells never touch `parent`.
 
 __device__ __forceinline__ int find_root(const int* parent, int x) {
     int p = __ldcg(parent + x);
@@ -134,7 +165,69 @@ __device__ __forceinline__ void unite(int* parent, int a, int b) {
     }
 }
 
-__global__ void k_ccl_merge(const uint32_t* __restrict__ bits_f, int* parent, Dims g, int conn) {
+__global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
+    const long long words = (long long)g.rows * g.W;
+    for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
+         gw += (long long)gridDim.x * blockDim.x) {
+        const uint32_t w = bits_f[gw];
+        if (!w) continue;
+        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const uint32_t carry = wi > 0 ? (bits_f[gw - 1] >> 31) : 0u;
+        const uint32_t starts = w & ~((w << 1) | carry);
+        const int x0 = row * g.nx + wi * 32;
+        uint32_t m = w;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const uint32_t below = starts & (b == 31 ? 0xffffffffu : ((2u << b) - 1u));
+            parent[x0 + b] = below ? x0 + (31 - __clz(below)) : x0 - 1;
+        }
+    }
+}
+
+// one union per maximal overlap segment of row `w` with neighbour row `wn`
+__device__ __forceinline__ void join_rows(int* parent, uint32_t w, uint32_t wn, uint32_t carry, int x0, int xn0) {
+    const uint32_t ov = w & wn;
+    uint32_t seg = ov & ~((ov << 1) | carry);
+    while (seg) {
+        const int b = __ffs(seg) - 1;
+        seg &= seg - 1u;
+        unite(parent, x0 + b, xn0 + b);
+    }
+}
+
+__global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
+    const long long words = (long long)g.rows * g.W;
+    for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
+         gw += (long long)gridDim.x * blockDim.x) {
+        const uint32_t w = bits_f[gw];
+        if (!w) continue;
+        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int j = row % g.ny, k = row / g.ny;
+        const int x0 = row * g.nx + wi * 32;
+        if (wi == 0 && (w & 1u) && g.nx > 1) {
+            const int last = g.nx - 1;
+            if ((bits_f[(size_t)row * g.W + (last >> 5)] >> (last & 31)) & 1u) unite(parent, x0, x0 + last);
+        }
+        const int rows_nb[2] = {k * g.ny + (j == 0 ? g.ny - 1 : j - 1), (k == 0 ? g.nz - 1 : k - 1) * g.ny + j};
+        for (int q = 0; q < 2; ++q) {
+            const int rn = rows_nb[q];
+            if (rn == row) continue;
+            const size_t gn = (size_t)rn * g.W + wi;
+            const uint32_t carry = wi > 0 ? ((bits_f[gw - 1] & bits_f[gn - 1]) >> 31) : 0u;
+            join_rows(parent, w, bits_f[gn], carry, x0, rn * g.nx + wi * 32);
+        }
+    }
+}
+
+__global__ void k_ccl_init(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        int i = x % g.nx, row = x / g.nx;
+        if (bit_at(bits_f, g.W, row, i)) parent[x] = x;
+    }
+}
+
+__global__ void k_ccl_merge26(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
         int i, j, k;
         decode(x, g, i, j, k);
@@ -142,11 +235,8 @@ __global__ void k_ccl_merge(const uint32_t* __restrict__ bits_f, int* parent, Di
         for (int dz = -1; dz <= 0; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
-                    // backward half of the neighbourhood
                     bool back = dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
                     if (!back) continue;
-                    int nnz = (dx != 0) + (dy != 0) + (dz != 0);
-                    if (conn == 6 && nnz != 1) continue;
                     int ii = wrapi(i + dx, g.nx), jj = wrapi(j + dy, g.ny), kk = wrapi(k + dz, g.nz);
                     if (!bit_at(bits_f, g.W, kk * g.ny + jj, ii)) continue;
                     unite(parent, x, cell(ii, jj, kk, g));
@@ -154,18 +244,33 @@ __global__ void k_ccl_merge(const uint32_t* __restrict__ bits_f, int* parent, Di
     }
 }
 
-__global__ void k_ccl_flatten(int* parent, int N) {
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        if (parent[x] >= 0) parent[x] = find_root(parent, x);
+__global__ void k_ccl_flatten(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
+    const long long words = (long long)g.rows * g.W;
+    for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
+         gw += (long long)gridDim.x * blockDim.x) {
+        uint32_t m = bits_f[gw];
+        if (!m) continue;
+        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int x0 = row * g.nx + wi * 32;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            parent[x0 + b] = find_root(parent, x0 + b);
+        }
     }
 }
 
 // Per block of 1024 cells: rank of each root among the block's roots.
-__global__ void __launch_bounds__(1024) k_ccl_count(const int* __restrict__ parent, int* __restrict__ rank,
-                                                    int* __restrict__ block_tot, int N) {
+__global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__ bits_f,
+                                                    const int* __restrict__ parent, int* __restrict__ rank,
+                                                    int* __restrict__ block_tot, Dims g) {
     __shared__ int warp_tot[32];
     int x = blockIdx.x * 1024 + threadIdx.x;
-    bool root = x < N && parent[x] == x;
+    bool root = false;
+    if (x < g.N) {
+        int i = x % g.nx, row = x / g.nx;
+        root = bit_at(bits_f, g.W, row, i) && parent[x] == x;
+    }
     unsigned m = __ballot_sync(0xffffffffu, root);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) warp_tot[wid] = __popc(m);
@@ -224,13 +329,27 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ to
     }
 }
 
-__global__ void k_ccl_relabel(const int* __restrict__ parent, const int* __restrict__ rank,
-                              const int* __restrict__ off, int* __restrict__ label, int* __restrict__ root_of,
-                              int root_cap, int N) {
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
-        int r = parent[x];
+cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st) {
+    k_scan_blocks<<<1, 1024, 0, st>>>(counts, off, n, nullptr);
+    return cudaGetLastError();
+}
+
+// Labels of one row segment per warp: 0 for empty cells, 1 + rank of the
+// root for occupied ones.
+__global__ void k_ccl_relabel(const uint32_t* __restrict__ bits_f, const int* __restrict__ parent,
+                              const int* __restrict__ rank, const int* __restrict__ off, int* __restrict__ label,
+                              int* __restrict__ root_of, int root_cap, Dims g) {
+    const int lane = threadIdx.x & 31;
+    const long long words = (long long)g.rows * g.W;
+    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < words;
+         gw += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int i = wi * 32 + lane;
+        if (i >= g.nx) continue;
+        const int x = row * g.nx + i;
         int l = 0;
-        if (r >= 0) {
+        if ((bits_f[gw] >> lane) & 1u) {
+            const int r = parent[x];
             l = off[r >> 10] + rank[r] + 1;
             if (r == x && root_of && l <= root_cap) root_of[l - 1] = x;
         }
@@ -242,13 +361,20 @@ cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* pa
                         int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
                         cudaStream_t st, long long* launches) {
     int nb = (g.N + 1023) / 1024;
-    int blocks = grid_for(g.N, 256);
-    k_ccl_init<<<blocks, 256, 0, st>>>(bits_f, parent, g);
-    k_ccl_merge<<<blocks, 256, 0, st>>>(bits_f, parent, g, conn);
-    k_ccl_flatten<<<blocks, 256, 0, st>>>(parent, g.N);
-    k_ccl_count<<<nb, 1024, 0, st>>>(parent, rank, block_tot, g.N);
+    long long words = (long long)g.rows * g.W;
+    int bw = grid_for(words, 256);
+    if (conn == 6) {
+        k_ccl_init_runs<<<bw, 256, 0, st>>>(bits_f, parent, g);
+        k_ccl_merge_runs<<<bw, 256, 0, st>>>(bits_f, parent, g);
+    } else {
+        k_ccl_init<<<grid_for(g.N, 256), 256, 0, st>>>(bits_f, parent, g);
+        k_ccl_merge26<<<grid_for(g.N, 256), 256, 0, st>>>(bits_f, parent, g);
+    }
+    k_ccl_flatten<<<bw, 256, 0, st>>>(bits_f, parent, g);
+    k_ccl_count<<<nb, 1024, 0, st>>>(bits_f, parent, rank, block_tot, g);
     k_scan_blocks<<<1, 1024, 0, st>>>(block_tot, block_off, nb, n_out);
-    k_ccl_relabel<<<blocks, 256, 0, st>>>(parent, rank, block_off, label, root_of, root_cap, g.N);
+    k_ccl_relabel<<<grid_for(words * 32, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
+                                                             root_cap, g);
     if (launches) *launches += 6;
     return cudaGetLastError();
 }

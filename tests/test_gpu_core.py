@@ -44,6 +44,7 @@ def make_case(shape, n_spheres, radius, seed, K=None, amp=0.5, drift=1.0, modes=
 
 
 def run_gpu(vof, c, u, dt, steps, precision=0, k_active=None, **kw):
+    kw.setdefault("tag_tau", 0.0)
     K, nz, ny, nx = c.shape
     dtp = torch.float64 if precision == 0 else torch.float32
     cfg = vof.make_config(nx, ny, nz, k_capacity=K, k_active=k_active or K, precision=precision, **kw)
@@ -151,6 +152,45 @@ def test_advect_mixed_matches_oracle(vof):
     assert np.abs(got - want).max() <= TOL32
     rel = abs(got.sum() - want.sum()) / want.sum()
     assert rel <= 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape,steps", [((36, 40, 32), 3), ((33, 20, 70), 2), ((5, 12, 40), 3),
+                                         ((64, 48, 48), 1)])
+def test_fused_mixed_steps(vof, shape, steps):
+    """The one-launch mixed step (ragged tiles, tiny z, every sweep order)
+    against the FP64 oracle run on the same float-rounded inputs."""
+    n = 6 if min(shape) > 8 else 3
+    r = 4.0 if min(shape) > 8 else 2.0
+    c, u, dt, _ = make_case(shape, n, r, seed=sum(shape) * 7 + steps, cfl=0.3)
+    c32 = c.astype(np.float32).astype(np.float64)
+    u32 = u.astype(np.float32).astype(np.float64)
+    ctx, c_d, _, rep = run_gpu(vof, c32, u32, dt, steps, precision=1)
+    want, clipped = O.advect(c32, u32, dt, 1.0, steps)
+    got = c_d.cpu().numpy().astype(np.float64)
+    assert np.abs(got - want).max() <= TOL32
+    assert abs(got.sum() - want.sum()) <= 1e-6 * want.sum()
+    assert rep["field_steps"] == steps * c.shape[0]
+    ctx.close()
+
+
+def test_fused_bits_feed_recolour(vof):
+    """Step 1 after a fused step uses the occupancy bits the step wrote; the
+    recolouring of the GPU's own field must equal the oracle's."""
+    shape = (40, 40, 40)
+    cen = synth.rsa_centres(shape, 4.0, 14, seed=48)
+    c = synth.coloured_fields(shape, cen, 4.0, np.zeros(14, dtype=np.int64), 4)
+    u = synth.solenoidal_velocity(shape, 8, 0.6, 0.5, 49)
+    dt = synth.dt_for_cfl(u, 0.3)
+    ctx, c_d, _, _ = run_gpu(vof, c, u, dt, 0, precision=1, k_active=1, tag_tau=1e-6)
+    na = 1
+    for s in range(3):
+        ctx.vof_step(dt, 1)
+        adv = c_d.cpu().numpy().astype(np.float64)
+        moved, na_g, st = ctx.vof_recolour()
+        want, na, nm, st_o, _ = O.recolour(adv, na, tau=1e-6)
+        assert (moved, na_g, st) == (nm, na, st_o)
+        assert np.array_equal(c_d.cpu().numpy().astype(np.float64), want)
     ctx.close()
 
 
@@ -269,6 +309,30 @@ def test_recolour_bit_exact(vof, seed):
     moved, na, st = ctx.vof_recolour()
     assert (moved, na, st) == (nm_o, na_o, st_o)
     assert np.array_equal(c_d.cpu().numpy(), want)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_recolour_with_threshold(vof, precision):
+    """tau = 1e-6: round-off residues below tau are not drops; the float path
+    decides c > tau exactly as the double comparison does."""
+    rng = np.random.default_rng(55 + precision)
+    shape = (18, 20, 40)
+    c = cubes(rng, shape, 4, 10)
+    resid = (rng.random(shape) < 0.05) * 10.0 ** rng.uniform(-12, -4, shape)
+    c[0] = np.where(c[0] == 0, resid, c[0])
+    c[0][0, 0, :4] = [1e-6, np.nextafter(1e-6, 1), float(np.float32(1e-6)), 2e-6]
+    if precision:
+        c = c.astype(np.float32).astype(np.float64)
+    want, na_o, nm_o, st_o, _ = O.recolour(c, 1, tau=1e-6)
+    ctx, c_d, _, _ = run_gpu(vof, c, np.zeros((3,) + shape), 0.0, 0, precision=precision, k_active=1,
+                             tag_tau=1e-6)
+    lab, n = ctx.vof_label(0)
+    lo, no = O.label(c[0], 1e-6)
+    assert n == no and np.array_equal(lab.cpu().numpy(), lo)
+    moved, na, st = ctx.vof_recolour()
+    assert (moved, na, st) == (nm_o, na_o, st_o)
+    assert np.array_equal(c_d.cpu().numpy().astype(np.float64), want)
     ctx.close()
 
 
