@@ -228,6 +228,79 @@ vof_status vof_plic_alpha(int32_t precision, const void *m_dev, const void *c_de
  * context's element type; zero where c <= 0 or c >= 1).  Asynchronous. */
 vof_status vof_normals(vof_ctx *ctx, int32_t field, void *m_dev);
 
+/*
+ * Learned normal estimator (no counterpart in the paper, which uses the PLIC
+ * normals this replaces): an MLP 27 -> 64 -> 64 -> 3 with ReLU, BF16 weights
+ * and activations, FP32 accumulation on the tensor cores, applied to the
+ * 3x3x3 stencil after reflecting it so that every Youngs component is >= 0
+ * and permuting its axes by increasing |Youngs component|; input c - 1/2.
+ * The weight blob (vof_mlp_weights_size() bytes, device memory) holds
+ * W1[64][32], W2[64][64], W3[16][64] (BF16, row = output, zero padding)
+ * and b1[64], b2[64], b3[16] (FP32).  Each input x enters as the BF16 pair
+ * hi = bf16(x), lo = bf16(x - hi), both multiplied by W1 (16 significant
+ * bits of c instead of 8).
+ */
+size_t vof_mlp_weights_size(void);
+
+/* Normals of n raw stencils (stencils_dev [n][27] float, order
+ * (k+1)*9+(j+1)*3+(i+1)) through the network: normals_dev [n][3] float,
+ * L2-normalised, pointing out of the c = 1 phase.  Synchronises `stream`;
+ * VOF_ERR_TIMEOUT if a tensor-core completion wait gave up. */
+vof_status vof_mlp_forward(const void *weights_dev, const float *stencils_dev, float *normals_dev,
+                           int64_t n, void *stream);
+
+/* Training on the GPU (forward and backward passes on the tensor cores,
+ * Adam on FP32 master weights, cosine learning-rate decay).  Samples are
+ * stencils of planes (normal uniform on the sphere, offset so the centre
+ * cell is cut, cell fractions from the exact PLIC volume) and of spheres
+ * (radius log-uniform in [r_min, r_max] cells, surface within 0.4 cells of
+ * the centre cell's centre, half of them inverted, cell fractions by
+ * quadrature); the target is the plane normal or the radial direction,
+ * pointing out of the c = 1 phase.  Loss 1 - cos(output, target). */
+typedef struct {
+    int64_t n_train;       /* training stencils (>= 128) */
+    int64_t n_test;        /* held-out stencils drawn with another seed */
+    int32_t epochs;
+    int32_t batch;         /* samples per Adam step, 128 .. 2^20, <= n_train */
+    float lr;              /* initial Adam step */
+    uint64_t seed;
+    float plane_fraction;  /* share of plane samples */
+    float r_min, r_max;    /* sphere radii in cells */
+} vof_train_params;
+
+typedef struct {
+    float final_loss;           /* mean loss over (up to 2^20) training samples */
+    int32_t steps;              /* Adam steps taken */
+    double test_mean_deg_mlp;   /* held-out mean angular error of the network */
+    double test_mean_deg_myc;   /* ... and of MYC on the same stencils */
+    double test_p95_deg_mlp;    /* held-out 95th percentiles */
+    double test_p95_deg_myc;
+    double test_mean_deg_combined; /* network with MYC fallback (residual judge, tol 1e-3) */
+    double test_p95_deg_combined;
+    double test_network_share;  /* share of held-out stencils that keep the network's normal */
+} vof_train_report;
+
+vof_status vof_mlp_train_params_default(vof_train_params *tp);
+size_t vof_mlp_train_workspace_size(const vof_train_params *tp);
+/* Train; weights_dev receives the blob.  Synchronises `stream`. */
+vof_status vof_mlp_train(const vof_train_params *tp, void *weights_dev, void *workspace_dev,
+                         size_t workspace_bytes, void *stream, vof_train_report *report);
+/* Gradient of the mean loss over n stencils (raw frame [n][27], unit targets
+ * [n][3]) with respect to the flat FP32 parameters W1[64][32], W2[64][64],
+ * W3[16][64], b1[64], b2[64], b3[16] (7312 values): grad_dev; loss_dev[0] =
+ * sum of the per-sample losses.  Synchronises `stream`. */
+vof_status vof_mlp_grad(const void *weights_dev, const float *stencils_dev, const float *targets_dev,
+                        int64_t n, float *grad_dev, float *loss_dev, void *stream);
+/* Flat FP32 parameters (order as vof_mlp_grad) -> weight blob.  Async. */
+vof_status vof_mlp_params_to_weights(const float *params_dev, void *weights_dev, void *stream);
+
+/* Instrumentation: D[128][n] = A[128][k] B[n][k]^T through one CTA's
+ * tensor-core path (operands rounded to BF16, FP32 result), to check the
+ * shared-memory operand layout; variant 1 swaps the descriptor's two byte
+ * offsets.  k, n in {16, 32, 64}.  Synchronises `stream`. */
+vof_status vof_tc_gemm_check(const float *a_dev, const float *b_dev, float *d_dev, int32_t k, int32_t n,
+                             int32_t variant, void *stream);
+
 /* Checkpoint: a self-describing blob of the fields, N(t), the step count
  * and the statistics accumulators.  vof_state_size gives its size. */
 size_t vof_state_size(const vof_ctx *ctx);

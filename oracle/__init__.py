@@ -86,6 +86,12 @@ def lib():
             L.oracle_pair_stats.argtypes = [_dp, C.c_int64, _dp, C.c_int, C.c_int, C.c_double,
                                             C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp,
                                             _dp]
+            L.oracle_canon.restype = None
+            L.oracle_canon.argtypes = [_dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.oracle_mlp_forward.restype = None
+            L.oracle_mlp_forward.argtypes = [_dp, _dp, C.c_int, _dp]
+            L.oracle_mlp_loss_grad.restype = C.c_double
+            L.oracle_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp]
             _lib = L
     return _lib
 
@@ -267,3 +273,41 @@ class PairStats:
     def A(self):
         R = self.R
         return R - np.trace(R) / 3.0 * np.eye(3)
+
+
+# --------------------------------------------------------------------------- learned normal
+
+MLP_NPARAM = 64 * 32 + 64 * 64 + 16 * 64 + 64 + 64 + 16
+
+
+def mlp_canon(st):
+    """(x[27], sign[3], perm[3]) of a stencil st[3][3][3] ([k][j][i])."""
+    x = np.zeros(27)
+    sg = (C.c_int * 3)()
+    pm = (C.c_int * 3)()
+    lib().oracle_canon(_f64(st).ravel(), x, sg, pm)
+    return x, list(sg), list(pm)
+
+
+def mlp_forward(params, x, bf16=True):
+    out = np.zeros(3)
+    lib().oracle_mlp_forward(_f64(params), _f64(x), int(bool(bf16)), out)
+    return out
+
+
+def mlp_normal(params, st, bf16=True):
+    """Network normal of a raw stencil, mapped back and L2-normalised."""
+    x, sg, pm = mlp_canon(st)
+    oc = mlp_forward(params, x, bf16)
+    n = np.zeros(3)
+    for q in range(3):
+        n[pm[q]] = sg[pm[q]] * oc[q]
+    return n / np.linalg.norm(n)
+
+
+def mlp_loss_grad(params, x, t, bf16=True):
+    x = _f64(x).reshape(-1, 27)
+    t = _f64(t).reshape(-1, 3)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().oracle_mlp_loss_grad(_f64(params), x, t, len(x), int(bool(bf16)), g)
+    return loss, g

@@ -828,3 +828,178 @@ void oracle_pair_stats(const double *cen, int64_t n, const double box[3], int ve
     free(dist);
     free(rv);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned normal estimator (MLP): canonical frame, forward, backprop       */
+
+#define MLP_IN 32
+#define MLP_HID 64
+#define MLP_OUTP 16
+#define MLP_NPARAM (MLP_HID * MLP_IN + MLP_HID * MLP_HID + MLP_OUTP * MLP_HID + MLP_HID + MLP_HID + MLP_OUTP)
+
+void oracle_canon(const double st[27], double x[27], int sign[3], int perm[3])
+{
+    double y[3];
+    youngs_raw(st, y);
+    double ay[3];
+    for (int a = 0; a < 3; ++a) {
+        sign[a] = y[a] < 0.0 ? -1 : 1;
+        ay[a] = fabs(y[a]);
+    }
+    /* stable order by |y|: an axis precedes another if smaller, ties by index */
+    int order[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (ay[order[j]] < ay[order[i]] ||
+                (ay[order[j]] == ay[order[i]] && order[j] < order[i])) {
+                int tmp = order[i];
+                order[i] = order[j];
+                order[j] = tmp;
+            }
+    for (int q = 0; q < 3; ++q)
+        perm[q] = order[q];
+    for (int kc = -1; kc <= 1; ++kc)
+        for (int jc = -1; jc <= 1; ++jc)
+            for (int ic = -1; ic <= 1; ++ic) {
+                int cv[3] = {ic, jc, kc}, o[3];
+                for (int q = 0; q < 3; ++q)
+                    o[perm[q]] = sign[perm[q]] * cv[q];
+                x[(kc + 1) * 9 + (jc + 1) * 3 + (ic + 1)] = ST(st, o[0], o[1], o[2]) - 0.5;
+            }
+}
+
+/* round to the nearest BF16 (ties to even) through the FP32 value */
+static double bf16r(double v)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7fffu + lsb;
+    b &= 0xffff0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+typedef struct {
+    const double *W1, *W2, *W3, *b1, *b2, *b3;
+} mlp_view;
+
+static mlp_view mlp_params(const double *p)
+{
+    mlp_view v;
+    v.W1 = p;
+    v.W2 = v.W1 + MLP_HID * MLP_IN;
+    v.W3 = v.W2 + MLP_HID * MLP_HID;
+    v.b1 = v.W3 + MLP_OUTP * MLP_HID;
+    v.b2 = v.b1 + MLP_HID;
+    v.b3 = v.b2 + MLP_HID;
+    return v;
+}
+
+/* forward keeping the pre-activations a1, a2 and the (rounded) layer
+ * inputs xin, h1, h2 */
+static void mlp_fwd_full(const double *params, const double x[27], int bf16, double xin[MLP_IN],
+                         double a1[MLP_HID], double h1[MLP_HID], double a2[MLP_HID], double h2[MLP_HID],
+                         double out[3])
+{
+    mlp_view w = mlp_params(params);
+    /* with bf16, an input enters as hi + lo: hi = bf16(x), lo = bf16(x - hi) */
+    for (int i = 0; i < MLP_IN; ++i) {
+        double v = i < 27 ? x[i] : 0.0;
+        if (bf16) {
+            double hi = bf16r(v);
+            double lo = bf16r((double)((float)v - (float)hi));
+            v = hi + lo;
+        }
+        xin[i] = v;
+    }
+    for (int o = 0; o < MLP_HID; ++o) {
+        double s = 0.0;
+        for (int i = 0; i < MLP_IN; ++i) {
+            double wv = bf16 ? bf16r(w.W1[o * MLP_IN + i]) : w.W1[o * MLP_IN + i];
+            s += wv * xin[i];
+        }
+        a1[o] = s + w.b1[o];
+        double h = a1[o] > 0.0 ? a1[o] : 0.0;
+        h1[o] = bf16 ? bf16r(h) : h;
+    }
+    for (int o = 0; o < MLP_HID; ++o) {
+        double s = 0.0;
+        for (int i = 0; i < MLP_HID; ++i) {
+            double wv = bf16 ? bf16r(w.W2[o * MLP_HID + i]) : w.W2[o * MLP_HID + i];
+            s += wv * h1[i];
+        }
+        a2[o] = s + w.b2[o];
+        double h = a2[o] > 0.0 ? a2[o] : 0.0;
+        h2[o] = bf16 ? bf16r(h) : h;
+    }
+    for (int o = 0; o < 3; ++o) {
+        double s = 0.0;
+        for (int i = 0; i < MLP_HID; ++i) {
+            double wv = bf16 ? bf16r(w.W3[o * MLP_HID + i]) : w.W3[o * MLP_HID + i];
+            s += wv * h2[i];
+        }
+        out[o] = s + w.b3[o];
+    }
+}
+
+void oracle_mlp_forward(const double *params, const double x[27], int bf16, double out[3])
+{
+    double xin[MLP_IN], a1[MLP_HID], h1[MLP_HID], a2[MLP_HID], h2[MLP_HID];
+    mlp_fwd_full(params, x, bf16, xin, a1, h1, a2, h2, out);
+}
+
+double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n, int bf16,
+                            double *grad)
+{
+    mlp_view w = mlp_params(params);
+    double *gW1 = grad, *gW2 = gW1 + MLP_HID * MLP_IN, *gW3 = gW2 + MLP_HID * MLP_HID;
+    double *gb1 = gW3 + MLP_OUTP * MLP_HID, *gb2 = gb1 + MLP_HID, *gb3 = gb2 + MLP_HID;
+    memset(grad, 0, sizeof(double) * MLP_NPARAM);
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        double xin[MLP_IN], a1[MLP_HID], h1[MLP_HID], a2[MLP_HID], h2[MLP_HID], out[3];
+        mlp_fwd_full(params, x + 27 * s, bf16, xin, a1, h1, a2, h2, out);
+        const double *ts = t + 3 * s;
+        double nrm = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+        double nh[3] = {out[0] / nrm, out[1] / nrm, out[2] / nrm};
+        double cs = nh[0] * ts[0] + nh[1] * ts[1] + nh[2] * ts[2];
+        loss += 1.0 - cs;
+        /* d(1 - nh.t)/d out = -(t - (nh.t) nh) / |out|, averaged over n */
+        double dy[3];
+        for (int o = 0; o < 3; ++o)
+            dy[o] = -(ts[o] - cs * nh[o]) / nrm / (double)n;
+        double dh2[MLP_HID], da2[MLP_HID], dh1[MLP_HID], da1[MLP_HID];
+        for (int o = 0; o < 3; ++o) {
+            gb3[o] += dy[o];
+            for (int i = 0; i < MLP_HID; ++i)
+                gW3[o * MLP_HID + i] += dy[o] * h2[i];
+        }
+        for (int i = 0; i < MLP_HID; ++i) {
+            double sacc = 0.0;
+            for (int o = 0; o < 3; ++o)
+                sacc += dy[o] * (bf16 ? bf16r(w.W3[o * MLP_HID + i]) : w.W3[o * MLP_HID + i]);
+            dh2[i] = sacc;
+            da2[i] = a2[i] > 0.0 ? dh2[i] : 0.0;
+        }
+        for (int o = 0; o < MLP_HID; ++o) {
+            gb2[o] += da2[o];
+            for (int i = 0; i < MLP_HID; ++i)
+                gW2[o * MLP_HID + i] += da2[o] * h1[i];
+        }
+        for (int i = 0; i < MLP_HID; ++i) {
+            double sacc = 0.0;
+            for (int o = 0; o < MLP_HID; ++o)
+                sacc += da2[o] * (bf16 ? bf16r(w.W2[o * MLP_HID + i]) : w.W2[o * MLP_HID + i]);
+            dh1[i] = sacc;
+            da1[i] = a1[i] > 0.0 ? dh1[i] : 0.0;
+        }
+        for (int o = 0; o < MLP_HID; ++o) {
+            gb1[o] += da1[o];
+            for (int i = 0; i < MLP_IN; ++i)
+                gW1[o * MLP_IN + i] += da1[o] * xin[i];
+        }
+    }
+    return loss / (double)n;
+}

@@ -102,6 +102,28 @@ void oracle_pair_stats(const double *cen, int64_t n, const double box[3],
                        double *hist_r, double *hist_rt, double *msum,
                        double *rsum, double *events);
 
+/* Learned normal (no counterpart in the paper): canonical frame of a
+ * stencil (reflect so every Youngs component is >= 0, axes ordered by
+ * increasing |Youngs component|, ties to the lower axis); x[27] = canonical
+ * stencil - 1/2.  sign[3], perm[3] describe the frame (canonical axis q is
+ * original axis perm[q]). */
+void oracle_canon(const double st[27], double x[27], int sign[3], int perm[3]);
+
+/* MLP 27 -> 64 -> 64 -> 3, ReLU.  Weights as the GPU blob in FP32:
+ * W1[64][32], W2[64][64], W3[16][64], b1[64], b2[64], b3[16] (flat, in that
+ * order; 7312 values).  With bf16 != 0, weights and the two hidden
+ * activations are rounded to BF16 (round to nearest even) and each input x
+ * becomes hi + lo with hi = bf16(x), lo = bf16(x - hi), as the tensor-core
+ * path does; everything else in FP64.  out[3] = canonical-frame output. */
+void oracle_mlp_forward(const double *params, const double x[27], int bf16, double out[3]);
+
+/* Loss 1 - cos(out, target) averaged over n canonical inputs x[n][27] with
+ * canonical unit targets t[n][3]; grad (7312 values, same order as params)
+ * receives d loss / d params (FP64 backprop through the same, optionally
+ * BF16-rounded, forward).  Returns the loss. */
+double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,
+                            int bf16, double *grad);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,15 @@ cudaError_t pair_stats(const double* cen, long long n, double bx, double by, dou
                        int n_rbins, double dr, int n_tbins, double dtheta, double tie_tol, double* hist_r,
                        double* hist_rt, double* moments, cudaStream_t st);
 
+// Learned normal estimator.
+struct MlpBlob;
+cudaError_t mlp_forward(const MlpBlob* w, const float* st, float* n_out, long long n, int* status,
+                        cudaStream_t stream);
+cudaError_t mlp_grad_pass(const MlpBlob* w, const float* st, const float* tgt, long long n0, long long n,
+                          float inv_batch, float* grad, float* loss_sum, int* status, cudaStream_t stream);
+cudaError_t tc_gemm_check(const float* A, const float* B, float* D, int K, int N, int swap, int* status,
+                          cudaStream_t st);
+
 // PLIC primitives and normals (tests and tools).
 cudaError_t plic_volume_batch(bool fp64, const void* m, const void* alpha, void* v, long long n,
                               cudaStream_t st);

@@ -44,6 +44,20 @@ class vof_step_report(C.Structure):
                 ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64)]
 
 
+class vof_train_params(C.Structure):
+    _fields_ = [("n_train", C.c_int64), ("n_test", C.c_int64), ("epochs", C.c_int32),
+                ("batch", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64),
+                ("plane_fraction", C.c_float), ("r_min", C.c_float), ("r_max", C.c_float)]
+
+
+class vof_train_report(C.Structure):
+    _fields_ = [("final_loss", C.c_float), ("steps", C.c_int32),
+                ("test_mean_deg_mlp", C.c_double), ("test_mean_deg_myc", C.c_double),
+                ("test_p95_deg_mlp", C.c_double), ("test_p95_deg_myc", C.c_double),
+                ("test_mean_deg_combined", C.c_double), ("test_p95_deg_combined", C.c_double),
+                ("test_network_share", C.c_double)]
+
+
 class vof_stats_out(C.Structure):
     _fields_ = [("n_drops", C.c_int32), ("d", C.c_double), ("n_p", C.c_double),
                 ("volume", C.c_double), ("events", C.c_double), ("M", C.c_double * 3),
@@ -57,7 +71,10 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_pair_stats", "vof_plic_volume", "vof_plic_alpha", "vof_normals",
            "vof_state_size", "vof_get_state", "vof_set_state", "vof_launch_count",
            "vof_status_string", "vof_destroy", "vof_profile_enable", "vof_profile_read",
-           "vof_profile_class_name", "vof_label_noalloc"]
+           "vof_profile_class_name", "vof_label_noalloc", "vof_mlp_weights_size",
+           "vof_mlp_forward", "vof_tc_gemm_check", "vof_mlp_train_params_default",
+           "vof_mlp_train_workspace_size", "vof_mlp_train", "vof_mlp_grad",
+           "vof_mlp_params_to_weights"]
 
 
 def lib():
@@ -95,6 +112,15 @@ def lib():
         "vof_profile_read": (C.c_int, [vp, vp, vp, i32]),
         "vof_profile_class_name": (C.c_char_p, [i32]),
         "vof_label_noalloc": (C.c_int, [vp, i32, i32, i32, i32, dbl, i32, vp, C.POINTER(i32), vp]),
+        "vof_mlp_weights_size": (C.c_size_t, []),
+        "vof_mlp_forward": (C.c_int, [vp, vp, vp, i64, vp]),
+        "vof_tc_gemm_check": (C.c_int, [vp, vp, vp, i32, i32, i32, vp]),
+        "vof_mlp_train_params_default": (C.c_int, [C.POINTER(vof_train_params)]),
+        "vof_mlp_train_workspace_size": (C.c_size_t, [C.POINTER(vof_train_params)]),
+        "vof_mlp_train": (C.c_int, [C.POINTER(vof_train_params), vp, vp, C.c_size_t, vp,
+                                    C.POINTER(vof_train_report)]),
+        "vof_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+        "vof_mlp_params_to_weights": (C.c_int, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -183,6 +209,74 @@ def vof_label_noalloc(c, precision=VOF_FP64, tag_tau=0.0, connectivity=6, out=No
     _check(lib().vof_label_noalloc(_ptr(c), precision, nx, ny, nz, float(tag_tau), connectivity,
                                    _ptr(out), C.byref(n), _stream(stream)), "vof_label_noalloc")
     return out, n.value
+
+
+def vof_mlp_forward(weights, stencils, stream=None):
+    """Normals [n][3] of raw stencils [n][27] (float32 device tensors)."""
+    import torch
+    n = stencils.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=stencils.device)
+    _check(lib().vof_mlp_forward(_ptr(weights), _ptr(stencils), _ptr(out), n, _stream(stream)),
+           "vof_mlp_forward")
+    return out
+
+
+MLP_NPARAM = 64 * 32 + 64 * 64 + 16 * 64 + 64 + 64 + 16
+
+
+def mlp_weights_empty(device="cuda"):
+    import torch
+    return torch.zeros(int(lib().vof_mlp_weights_size()), dtype=torch.uint8, device=device)
+
+
+def vof_mlp_params_to_weights(params, weights=None, stream=None):
+    """Flat FP32 parameters (device tensor, 7312 values) -> weight blob."""
+    if weights is None:
+        weights = mlp_weights_empty(params.device)
+    _check(lib().vof_mlp_params_to_weights(_ptr(params), _ptr(weights), _stream(stream)),
+           "vof_mlp_params_to_weights")
+    return weights
+
+
+def vof_mlp_grad(weights, stencils, targets, stream=None):
+    import torch
+    g = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=stencils.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=stencils.device)
+    _check(lib().vof_mlp_grad(_ptr(weights), _ptr(stencils), _ptr(targets), stencils.shape[0], _ptr(g),
+                              _ptr(loss), _stream(stream)), "vof_mlp_grad")
+    return g, float(loss.item())
+
+
+def train_params(**kw):
+    tp = vof_train_params()
+    _check(lib().vof_mlp_train_params_default(C.byref(tp)), "vof_mlp_train_params_default")
+    for k, v in kw.items():
+        setattr(tp, k, v)
+    return tp
+
+
+def vof_mlp_train(tp, device="cuda", stream=None):
+    """Train on the GPU; returns (weight blob tensor, report dict)."""
+    import torch
+    nbytes = int(lib().vof_mlp_train_workspace_size(C.byref(tp)))
+    if nbytes == 0:
+        raise VofError(-1, "vof_mlp_train_workspace_size")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    w = mlp_weights_empty(device)
+    rep = vof_train_report()
+    _check(lib().vof_mlp_train(C.byref(tp), _ptr(w), _ptr(ws), nbytes, _stream(stream), C.byref(rep)),
+           "vof_mlp_train")
+    del ws
+    return w, {k: getattr(rep, k) for k, _ in vof_train_report._fields_}
+
+
+def vof_tc_gemm_check(a, b, variant=0, stream=None):
+    import torch
+    n, k = b.shape
+    d = torch.empty((128, n), dtype=torch.float32, device=a.device)
+    _check(lib().vof_tc_gemm_check(_ptr(a), _ptr(b), _ptr(d), k, n, variant, _stream(stream)),
+           "vof_tc_gemm_check")
+    return d
 
 
 # --------------------------------------------------------------------------- context
