@@ -104,6 +104,8 @@ typedef struct {
     int32_t n_moved;           /* drops moved by Step 4 during the call */
     int32_t near_contact_steps;/* steps whose Step 1 fired somewhere */
     int64_t field_steps;       /* sum over the call's steps of fields advected */
+    int64_t faces_network;     /* VOF_MIXED_LEARNED: interfacial faces on the network's normal */
+    int64_t faces_myc;         /* ... and on MYC's normal (the fallback) */
 } vof_step_report;
 
 /*
@@ -119,6 +121,23 @@ typedef struct {
  * when recolouring is off and report is NULL.
  */
 vof_status vof_step(vof_ctx *ctx, double dt, int32_t nsteps, vof_step_report *report);
+
+/*
+ * Learned normal for a VOF_MIXED_LEARNED context (no counterpart in the
+ * paper; it replaces the MYC normal of Section 2.2 in the FP32 fluxes).
+ * weights_dev: device blob of vof_mlp_weights_size() bytes (see
+ * vof_mlp_forward), 16-byte aligned, borrowed until the context is
+ * destroyed or the next vof_set_mlp.  In every listed donor stencil the
+ * network's normal is kept when the mean residual over the 27 cells of its
+ * plane (through the centre cell's fraction, extended over the block) is at
+ * most fallback_tol (1e-3 by default) or no larger than MYC's; otherwise
+ * MYC's normal is used.  VOF_ERR_ARG for another precision, a null or
+ * unaligned blob, or a negative / non-finite tolerance.  vof_step on a
+ * VOF_MIXED_LEARNED context without weights returns VOF_ERR_STATE; a
+ * timed-out tensor-core wait is reported as VOF_ERR_TIMEOUT by the next
+ * vof_step with a report.
+ */
+vof_status vof_set_mlp(vof_ctx *ctx, const void *weights_dev, double fallback_tol);
 
 /* Step 1 for every active field: flags_host[k] = 1 if field k has a cell
  * with c <= tau whose (2w+1)^3 stencil holds two opposite cells with
@@ -248,6 +267,18 @@ size_t vof_mlp_weights_size(void);
  * VOF_ERR_TIMEOUT if a tensor-core completion wait gave up. */
 vof_status vof_mlp_forward(const void *weights_dev, const float *stencils_dev, float *normals_dev,
                            int64_t n, void *stream);
+
+/* The learned normal exactly as the VOF_MIXED_LEARNED step applies it to a
+ * donor stencil (see vof_set_mlp): network, mapped back from the canonical
+ * frame, kept when its 27-cell mean residual is <= fallback_tol or no larger
+ * than MYC's, else MYC's normal.  stencils_dev float [n][27] as in
+ * vof_mlp_forward; normals_dev float [n][3] receives the L1-normalised
+ * choice, which_dev int32 [n] 0 (network) or 1 (MYC).  Synchronises
+ * `stream`.  VOF_ERR_ARG on a bad pointer, n < 0 or a negative tolerance;
+ * VOF_ERR_TIMEOUT on a timed-out tensor-core wait. */
+vof_status vof_learned_normals(const void *weights_dev, const float *stencils_dev, int64_t n,
+                               double fallback_tol, float *normals_dev, int32_t *which_dev,
+                               void *stream);
 
 /* Training on the GPU (forward and backward passes on the tensor cores,
  * Adam on FP32 master weights, cosine learning-rate decay).  Samples are

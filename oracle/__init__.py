@@ -90,6 +90,16 @@ def lib():
             L.oracle_canon.argtypes = [_dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.oracle_mlp_forward.restype = None
             L.oracle_mlp_forward.argtypes = [_dp, _dp, C.c_int, _dp]
+            L.oracle_normal_residual.restype = C.c_double
+            L.oracle_normal_residual.argtypes = [_dp, _dp]
+            L.oracle_learned_normal.restype = C.c_int
+            L.oracle_learned_normal.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_int, _dp,
+                                                C.POINTER(C.c_int)]
+            L.oracle_advect_step_learned.restype = C.c_int
+            L.oracle_advect_step_learned.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                     C.c_double, C.c_double, C.c_int64, _dp,
+                                                     C.c_double, C.c_double, C.c_int, _dp,
+                                                     C.POINTER(C.c_int64), C.c_void_p]
             L.oracle_mlp_loss_grad.restype = C.c_double
             L.oracle_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp]
             _lib = L
@@ -158,6 +168,43 @@ def advect_step(c, u, dt, h, step_index):
     if rc != 0:
         raise MemoryError("oracle_advect_step")
     return (c[0] if squeeze else c), clipped
+
+
+def advect_step_learned(c, u, dt, h, step_index, params, tol=1e-3, amb_eps=1e-6, amb_choice=0,
+                        amb_map=None):
+    """One step with the learned normal (MYC fallback); returns (c_new,
+    clipped[K], counts) with counts = (faces on the network, on MYC,
+    ambiguous decisions resolved by amb_choice).  amb_map (uint8 array of
+    c's shape, optional) gets 1 on both cells of every ambiguous face."""
+    c = np.array(c, dtype=np.float64, order="C", copy=True)
+    squeeze = c.ndim == 3
+    if squeeze:
+        c = c[None]
+    K, nz, ny, nx = c.shape
+    clipped = np.zeros(K)
+    counts = (C.c_int64 * 3)()
+    rc = lib().oracle_advect_step_learned(c, _f64(u), nx, ny, nz, K, float(dt), float(h),
+                                          int(step_index), _f64(params), float(tol), float(amb_eps),
+                                          int(amb_choice), clipped, counts,
+                                          None if amb_map is None else amb_map.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle_advect_step_learned")
+    return (c[0] if squeeze else c), clipped, tuple(counts)
+
+
+def normal_residual(st, n):
+    """Mean residual over the 27 cells of the plane of normal n through the
+    centre cell (judge of the learned normal)."""
+    return lib().oracle_normal_residual(_f64(np.asarray(st).reshape(27)), _f64(n))
+
+
+def learned_normal(params, st, tol=1e-3, amb_eps=0.0, amb_choice=0):
+    """(m, which, ambiguous): L1-normalised normal, 0 = network / 1 = MYC."""
+    m = np.zeros(3)
+    amb = C.c_int(0)
+    which = lib().oracle_learned_normal(_f64(params), _f64(np.asarray(st).reshape(27)), float(tol),
+                                        float(amb_eps), int(amb_choice), m, C.byref(amb))
+    return m, which, amb.value
 
 
 def advect(c, u, dt, h, steps, first_step=0):

@@ -308,8 +308,17 @@ static void gather_stencil(const double *c, int nx, int ny, int nz, int i, int j
                 ST(st, e, a, b) = c[idx3(wrap(i + e, nx), wrap(j + a, ny), wrap(k + b, nz), nx, ny)];
 }
 
-double oracle_cell_face_flux(const double *c, int nx, int ny, int nz, int i, int j,
-                             int k, int d, double s)
+/* Learned-normal settings of a step (NULL: MYC everywhere). */
+typedef struct {
+    const double *params;
+    double tol, amb_eps;
+    int amb_choice;
+    int64_t counts[3]; /* faces on the network, on MYC, decided as ambiguous */
+    uint8_t *amb_map;  /* current field's map of cells next to ambiguous faces, or NULL */
+} learned_cfg;
+
+static double cell_face_flux(const double *c, int nx, int ny, int nz, int i, int j, int k, int d,
+                             double s, learned_cfg *L)
 {
     if (s == 0.0)
         return 0.0;
@@ -327,13 +336,38 @@ double oracle_cell_face_flux(const double *c, int nx, int ny, int nz, int i, int
         return s;
     double st[27], m[3];
     gather_stencil(c, nx, ny, nz, si, sj, sk, st);
-    oracle_myc(st, m);
-    double alpha = oracle_plic_alpha(m, cd);
-    return oracle_face_flux(m, alpha, d, s);
+    if (!L) {
+        oracle_myc(st, m);
+        return oracle_face_flux(m, oracle_plic_alpha(m, cd), d, s);
+    }
+    int amb = 0;
+    int which = oracle_learned_normal(L->params, st, L->tol, L->amb_eps, L->amb_choice, m, &amb);
+    L->counts[which] += 1;
+    L->counts[2] += amb;
+    double F = oracle_face_flux(m, oracle_plic_alpha(m, cd), d, s);
+    if (amb && L->amb_map) {
+        /* an ambiguous decision matters only where the other branch gives
+         * another flux: mark both cells of the face then */
+        double m2[3];
+        oracle_learned_normal(L->params, st, L->tol, L->amb_eps, 1 - L->amb_choice, m2, NULL);
+        double F2 = oracle_face_flux(m2, oracle_plic_alpha(m2, cd), d, s);
+        if (fabs(F2 - F) > 1e-7) {
+            L->amb_map[idx3(i, j, k, nx, ny)] = 1;
+            L->amb_map[idx3(si, sj, sk, nx, ny)] = 1;
+        }
+    }
+    return F;
 }
 
-int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz, int K,
-                       double dt, double h, int64_t step_index, double *clipped)
+double oracle_cell_face_flux(const double *c, int nx, int ny, int nz, int i, int j,
+                             int k, int d, double s)
+{
+    return cell_face_flux(c, nx, ny, nz, i, j, k, d, s, NULL);
+}
+
+static int advect_step(double *c, const double *u, int nx, int ny, int nz, int K, double dt,
+                       double h, int64_t step_index, double *clipped, learned_cfg *L,
+                       uint8_t *L_map)
 {
     int64_t N = (int64_t)nx * ny * nz;
     double sfac = dt / h;
@@ -356,11 +390,13 @@ int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz, int K
         for (int f = 0; f < K; ++f) {
             double *cf = c + (int64_t)f * N;
             const double *ccf = cc + (int64_t)f * N;
+            if (L)
+                L->amb_map = L_map ? L_map + (int64_t)f * N : NULL;
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < ny; ++j)
                     for (int i = 0; i < nx; ++i) {
                         int64_t x = idx3(i, j, k, nx, ny);
-                        F[x] = oracle_cell_face_flux(cf, nx, ny, nz, i, j, k, d, ud[x] * sfac);
+                        F[x] = cell_face_flux(cf, nx, ny, nz, i, j, k, d, ud[x] * sfac, L);
                     }
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < ny; ++j)
@@ -391,6 +427,25 @@ int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz, int K
     free(F);
     free(nw);
     return 0;
+}
+
+int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz, int K,
+                       double dt, double h, int64_t step_index, double *clipped)
+{
+    return advect_step(c, u, nx, ny, nz, K, dt, h, step_index, clipped, NULL, NULL);
+}
+
+int oracle_advect_step_learned(double *c, const double *u, int nx, int ny, int nz, int K,
+                               double dt, double h, int64_t step_index, const double *params,
+                               double tol, double amb_eps, int amb_choice, double *clipped,
+                               int64_t counts[3], uint8_t *amb_map)
+{
+    learned_cfg L = {params, tol, amb_eps, amb_choice, {0, 0, 0}, NULL};
+    int r = advect_step(c, u, nx, ny, nz, K, dt, h, step_index, clipped, &L, amb_map);
+    if (counts)
+        for (int q = 0; q < 3; ++q)
+            counts[q] = L.counts[q];
+    return r;
 }
 
 void oracle_normals(const double *c, int nx, int ny, int nz, double *m_out)
@@ -881,6 +936,14 @@ static double bf16r(double v)
     return (double)f;
 }
 
+/* a layer input as the tensor-core path feeds it: the pair hi = bf16(v),
+ * lo = bf16(v - hi), which carries about 16 significant bits of v */
+static double bf16_pair(double v)
+{
+    double hi = bf16r(v);
+    return hi + bf16r((double)((float)v - (float)hi));
+}
+
 typedef struct {
     const double *W1, *W2, *W3, *b1, *b2, *b3;
 } mlp_view;
@@ -904,15 +967,9 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
                          double out[3])
 {
     mlp_view w = mlp_params(params);
-    /* with bf16, an input enters as hi + lo: hi = bf16(x), lo = bf16(x - hi) */
     for (int i = 0; i < MLP_IN; ++i) {
         double v = i < 27 ? x[i] : 0.0;
-        if (bf16) {
-            double hi = bf16r(v);
-            double lo = bf16r((double)((float)v - (float)hi));
-            v = hi + lo;
-        }
-        xin[i] = v;
+        xin[i] = bf16 ? bf16_pair(v) : v;
     }
     for (int o = 0; o < MLP_HID; ++o) {
         double s = 0.0;
@@ -922,7 +979,7 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
         }
         a1[o] = s + w.b1[o];
         double h = a1[o] > 0.0 ? a1[o] : 0.0;
-        h1[o] = bf16 ? bf16r(h) : h;
+        h1[o] = bf16 ? bf16_pair(h) : h;
     }
     for (int o = 0; o < MLP_HID; ++o) {
         double s = 0.0;
@@ -932,7 +989,7 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
         }
         a2[o] = s + w.b2[o];
         double h = a2[o] > 0.0 ? a2[o] : 0.0;
-        h2[o] = bf16 ? bf16r(h) : h;
+        h2[o] = bf16 ? bf16_pair(h) : h;
     }
     for (int o = 0; o < 3; ++o) {
         double s = 0.0;
@@ -948,6 +1005,57 @@ void oracle_mlp_forward(const double *params, const double x[27], int bf16, doub
 {
     double xin[MLP_IN], a1[MLP_HID], h1[MLP_HID], a2[MLP_HID], h2[MLP_HID];
     mlp_fwd_full(params, x, bf16, xin, a1, h1, a2, h2, out);
+}
+
+double oracle_normal_residual(const double st[27], const double n[3])
+{
+    double l1 = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
+    if (!(l1 > 0.0) || !isfinite(l1))
+        return INFINITY;
+    double m[3] = {n[0] / l1, n[1] / l1, n[2] / l1};
+    double alpha = oracle_plic_alpha(m, ST(st, 0, 0, 0));
+    double e = 0.0;
+    for (int k = -1; k <= 1; ++k)
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+                /* the plane m.x = alpha of the centre cell [0,1]^3, seen from
+                 * the cell at offset (i,j,k): m.(x' + o) = alpha */
+                double v = oracle_plic_volume(m, alpha - (m[0] * i + m[1] * j + m[2] * k));
+                e += fabs(v - ST(st, i, j, k));
+            }
+    return e / 27.0;
+}
+
+int oracle_learned_normal(const double *params, const double st[27], double tol, double amb_eps,
+                          int amb_choice, double m[3], int *ambiguous)
+{
+    double x[27], oc[3], n[3], mm[3];
+    int sign[3], perm[3];
+    oracle_canon(st, x, sign, perm);
+    oracle_mlp_forward(params, x, 1, oc);
+    for (int q = 0; q < 3; ++q)
+        n[perm[q]] = sign[perm[q]] * oc[q];
+    oracle_myc(st, mm);
+    double e_net = oracle_normal_residual(st, n);
+    double e_myc = oracle_normal_residual(st, mm);
+    double thr = e_myc > tol ? e_myc : tol;
+    int use_myc = !(e_net <= thr); /* also for a non-finite network output */
+    int amb = isfinite(e_net) && fabs(e_net - thr) <= amb_eps;
+    if (amb)
+        use_myc = amb_choice;
+    if (ambiguous)
+        *ambiguous = amb;
+    if (use_myc) {
+        m[0] = mm[0];
+        m[1] = mm[1];
+        m[2] = mm[2];
+        return 1;
+    }
+    double l1 = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
+    m[0] = n[0] / l1;
+    m[1] = n[1] / l1;
+    m[2] = n[2] / l1;
+    return 0;
 }
 
 double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n, int bf16,

@@ -111,11 +111,39 @@ void oracle_canon(const double st[27], double x[27], int sign[3], int perm[3]);
 
 /* MLP 27 -> 64 -> 64 -> 3, ReLU.  Weights as the GPU blob in FP32:
  * W1[64][32], W2[64][64], W3[16][64], b1[64], b2[64], b3[16] (flat, in that
- * order; 7312 values).  With bf16 != 0, weights and the two hidden
- * activations are rounded to BF16 (round to nearest even) and each input x
- * becomes hi + lo with hi = bf16(x), lo = bf16(x - hi), as the tensor-core
- * path does; everything else in FP64.  out[3] = canonical-frame output. */
+ * order; 7312 values).  With bf16 != 0, weights are rounded to BF16 (round
+ * to nearest even) and every layer input v (the 27 stencil values and the
+ * two hidden activations) becomes hi + lo with hi = bf16(v),
+ * lo = bf16(v - hi), as the tensor-core path does; everything else in FP64.
+ * out[3] = canonical-frame output. */
 void oracle_mlp_forward(const double *params, const double x[27], int bf16, double out[3]);
+
+/* Residual of a normal on a stencil (judge of the learned normal): the
+ * plane of normal n through the centre cell with the centre's fraction,
+ * extended over the 3x3x3 block; mean over the 27 cells of
+ * |plane volume - c|.  +inf for a zero or non-finite n. */
+double oracle_normal_residual(const double st[27], const double n[3]);
+
+/* Learned normal with MYC fallback: the network's normal (mapped back from
+ * the canonical frame, BF16 forward as above) unless it is non-finite or
+ * its residual exceeds max(tol, residual of MYC's normal), then MYC's.
+ * When the residual lies within amb_eps of that threshold the decision is
+ * ambiguous between implementations that compute it in other precisions:
+ * *ambiguous = 1 and amb_choice (0 network, 1 MYC) decides.  m receives the
+ * L1-normalised normal; returns 0 (network) or 1 (MYC). */
+int oracle_learned_normal(const double *params, const double st[27], double tol, double amb_eps,
+                          int amb_choice, double m[3], int *ambiguous);
+
+/* oracle_advect_step with oracle_learned_normal in place of MYC for every
+ * interfacial donor.  counts[3] (may be NULL) receives the faces on the
+ * network, on MYC, and how many of them were ambiguous decisions; amb_map
+ * ([K][nz][ny][nx] bytes, may be NULL, not cleared) gets 1 on both cells of
+ * every face whose decision was ambiguous and whose flux under the other
+ * branch differs by more than 1e-7. */
+int oracle_advect_step_learned(double *c, const double *u, int nx, int ny, int nz, int K,
+                               double dt, double h, int64_t step_index, const double *params,
+                               double tol, double amb_eps, int amb_choice, double *clipped,
+                               int64_t counts[3], uint8_t *amb_map);
 
 /* Loss 1 - cos(out, target) averaged over n canonical inputs x[n][27] with
  * canonical unit targets t[n][3]; grad (7312 values, same order as params)

@@ -5,7 +5,9 @@
 //   face_flux  one thread per listed face whose upwind donor is interfacial
 //              (0 < c < 1): MYC normal and plane constant of the donor, PLIC
 //              volume of the swept sub-cell.  Listing keeps the costly
-//              reconstruction on full warps.
+//              reconstruction on full warps.  With a learned normal the FP32
+//              path runs face_flux_learned instead (tiles of 128 listed
+//              faces through the network on the tensor cores).
 //   update     one warp per 32-cell row segment, looping over the fields so
 //              the velocity is read once: c <- c - (F_hi - F_lo) +
 //              c_c (s_hi - s_lo) with c_c = [c > 1/2] at the step's start
@@ -20,6 +22,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -51,6 +54,11 @@ struct AdvectArgs {
     cudaStream_t stream;
     long long* launches;
     Prof* prof;
+    // learned normal (FP32 path only; null = MYC everywhere)
+    const MlpBlob* mlp;
+    float mlp_tol;                       // residual below which the network is kept outright
+    int* mlp_status;                     // set on a timed-out tensor-core wait
+    unsigned long long* mlp_counters;    // [0] faces on the network's normal, [1] on MYC's
 };
 
 template <typename T>
@@ -356,15 +364,24 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
             const int cur = a.list_cur, nxt = 1 - a.list_cur;
             if (a.prof) a.prof->begin(P_FACE_FLUX);
             scan_counts(counts[cur], a.offsets, gb, a.stream);
-            k_face_flux<T><<<152 * 16, 128, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur], cap,
-                                                            a.offsets, gb, fl);
+            bool learned = false;
+            if constexpr (std::is_same<T, float>::value) {
+                if (a.mlp) {
+                    learned = true;
+                    face_flux_learned(ins[sw], ud, g, d, sfac, band, lists[cur], cap, a.offsets, gb, fl, a.mlp,
+                                      a.mlp_tol, a.mlp_status, a.mlp_counters, a.stream);
+                }
+            }
+            if (!learned)
+                k_face_flux<T><<<152 * 16, 128, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur], cap,
+                                                                a.offsets, gb, fl);
             if (a.prof) { a.prof->end(); a.prof->begin(P_UPDATE); }
             k_update<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac, tau, fl,
                                                              a.ccbits, a.occbits, lists[nxt], cap, counts[nxt],
                                                              a.clipped);
             if (a.prof) a.prof->end();
             a.list_cur = nxt;
-            if (a.launches) *a.launches += 2;
+            if (a.launches) *a.launches += 3;  // scan, flux, update
         }
         a.list_valid = true;
     }

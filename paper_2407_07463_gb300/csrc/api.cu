@@ -46,14 +46,16 @@ enum Slot {
 };
 
 // MISC slot layout (bytes): counters[8] u64 | flags[16] int | clipped[16] double |
-// overflow int | n_out[16] int | vscan[2] u64
+// overflow int | n_out[16] int | vscan[2] u64 | learned-normal status int, face counters[2] u64
 constexpr size_t kMiscCounters = 0;
 constexpr size_t kMiscFlags = 64;
 constexpr size_t kMiscClipped = 128;
 constexpr size_t kMiscOverflow = 256;
 constexpr size_t kMiscNout = 320;
 constexpr size_t kMiscVscan = 448;
-constexpr size_t kMiscBytes = 512;
+constexpr size_t kMiscMlpStatus = 512;
+constexpr size_t kMiscMlpCounters = 576;
+constexpr size_t kMiscBytes = 640;
 constexpr int kMaxK = 16;
 constexpr int kMoveWords = (kMoveCap + 31) / 32;
 
@@ -153,6 +155,8 @@ struct vof_ctx {
     vof_status sticky;
     long long launches;
     Prof prof;
+    const void* mlp;  // borrowed weight blob of the learned normal (VOF_MIXED_LEARNED)
+    double mlp_tol;
 
     template <typename P>
     P* slot(int s) const { return (P*)(ws + L.off[s]); }
@@ -432,6 +436,8 @@ vof_status vof_init(const vof_config* cfg, void* c_dev, const void* u_dev, void*
     ctx->sticky = VOF_OK;
     ctx->launches = 0;
     ctx->prof.st = ctx->stream;
+    ctx->mlp = nullptr;
+    ctx->mlp_tol = 1e-3;
     if (cudaMemsetAsync(ctx->ws + L.off[S_MISC], 0, kMiscBytes, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_R], 0, L.size[S_HIST_R], ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_RT], 0, L.size[S_HIST_RT], ctx->stream) != cudaSuccess ||
@@ -457,13 +463,29 @@ vof_status vof_set_velocity(vof_ctx* ctx, const void* u_dev) {
     return scan_velocity(ctx);
 }
 
+vof_status vof_set_mlp(vof_ctx* ctx, const void* weights_dev, double fallback_tol) {
+    vof_status s = check_ctx(ctx);
+    if (s != VOF_OK) return s;
+    if (ctx->cfg.precision != VOF_MIXED_LEARNED || !weights_dev || ((uintptr_t)weights_dev & 15) != 0 ||
+        !(fallback_tol >= 0.0) || !std::isfinite(fallback_tol))
+        return VOF_ERR_ARG;
+    ctx->mlp = weights_dev;
+    ctx->mlp_tol = fallback_tol;
+    return VOF_OK;
+}
+
 vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* report) {
     vof_status s = check_ctx(ctx);
     if (s != VOF_OK) return s;
     if (!(dt >= 0.0) || !std::isfinite(dt) || nsteps < 0) return VOF_ERR_ARG;
     if (ctx->umax * dt / ctx->cfg.h > 0.5) return VOF_ERR_CFL;
+    if (ctx->cfg.precision == VOF_MIXED_LEARNED && !ctx->mlp) return VOF_ERR_STATE;
     double* clipped = (double*)(ctx->misc() + kMiscClipped);
-    if (report) VOF_CUDA(ctx, cudaMemsetAsync(clipped, 0, kMaxK * sizeof(double), ctx->stream));
+    unsigned long long* mlp_counters = (unsigned long long*)(ctx->misc() + kMiscMlpCounters);
+    if (report) {
+        VOF_CUDA(ctx, cudaMemsetAsync(clipped, 0, kMaxK * sizeof(double), ctx->stream));
+        VOF_CUDA(ctx, cudaMemsetAsync(mlp_counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    }
     AdvectArgs a;
     a.g = ctx->g;
     a.c = ctx->c;
@@ -487,6 +509,10 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     a.stream = ctx->stream;
     a.launches = &ctx->launches;
     a.prof = &ctx->prof;
+    a.mlp = (const MlpBlob*)ctx->mlp;
+    a.mlp_tol = (float)ctx->mlp_tol;
+    a.mlp_status = (int*)(ctx->misc() + kMiscMlpStatus);
+    a.mlp_counters = mlp_counters;
     int moved_total = 0, fired_steps = 0;
     long long field_steps = 0;
     vof_status result = VOF_OK;
@@ -511,8 +537,15 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     }
     if (report) {
         double hc[kMaxK];
+        unsigned long long hm[2];
+        int mst = 0;
         VOF_CUDA(ctx, cudaMemcpyAsync(hc, clipped, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+        VOF_CUDA(ctx, cudaMemcpyAsync(hm, mlp_counters, sizeof(hm), cudaMemcpyDeviceToHost, ctx->stream));
+        VOF_CUDA(ctx, cudaMemcpyAsync(&mst, a.mlp_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         VOF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (mst) return ctx->sticky = VOF_ERR_TIMEOUT;
+        report->faces_network = (int64_t)hm[0];
+        report->faces_myc = (int64_t)hm[1];
         double tot = 0.0;
         for (int f = 0; f < ctx->cfg.k_capacity; ++f) tot += hc[f];
         report->steps_done = ctx->step;

@@ -55,6 +55,11 @@ constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
 constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a sweep
 
 struct AdvectArgs;
+struct MlpBlob;
+// Learned-normal face fluxes of the listed faces of one sweep (FP32 path).
+void face_flux_learned(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
+                       const unsigned long long* list, long long cap, const int* off, int nseg, float* flux,
+                       const MlpBlob* w, float tol, int* status, unsigned long long* counters, cudaStream_t st);
 cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps);
 cudaError_t advect_steps_fp32(AdvectArgs& a, int nsteps);
 

@@ -1,7 +1,7 @@
 // Learned interface normal: an MLP 27 -> 64 -> 64 -> 3 (ReLU) on the
-// canonicalised 3x3x3 volume-fraction stencil, BF16 weights and activations,
-// FP32 accumulation in tensor memory (tcgen05), used in place of MYC with
-// MYC as the fallback.  (No counterpart in the paper; the paper's PLIC
+// canonicalised 3x3x3 volume-fraction stencil, BF16 weights, every layer
+// input as a BF16 (hi, lo) pair, FP32 accumulation in tensor memory
+// (tcgen05), used in place of MYC with MYC as the fallback.  (No counterpart in the paper; the paper's PLIC
 // normals are the method it replaces.)
 //
 // Canonical frame: the stencil is reflected so that every Youngs component
@@ -12,10 +12,12 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "internal.h"
 #include "mlp.cuh"
+#include "mlp_tile.cuh"
 #include "plic.cuh"
 #include "tc.cuh"
 
@@ -80,147 +82,6 @@ cudaError_t tc_gemm_check(const float* A, const float* B, float* D, int K, int N
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// one CTA-wide forward pass over a tile of 128 canonical inputs
-
-// Shared-memory image of the network plus activation tiles.
-struct MlpSmem {
-    unsigned char X[128 * kInHL * 2];    // 128 x 64 (hi | lo)
-    unsigned char H[128 * kHid * 2];     // 128 x 64
-    unsigned char W1[kHid * kInHL * 2];  // 64 x 64 (W1 | W1)
-    unsigned char W2[kHid * kHid * 2];   // 64 x 64
-    unsigned char W3[kOutP * kHid * 2];  // 16 x 64
-    float b1[kHid], b2[kHid], b3[kOutP];
-    uint64_t bar;
-    uint32_t tbase;
-    int timeout;
-};
-
-__device__ void load_weights(MlpSmem& s, const MlpBlob* __restrict__ w) {
-    for (int idx = threadIdx.x; idx < kHid * kIn; idx += blockDim.x) {
-        const int o = idx / kIn, i = idx % kIn;
-        *reinterpret_cast<__nv_bfloat16*>(s.W1 + tc::kmajor_offset(o, i, kInHL)) = w->W1[idx];
-        *reinterpret_cast<__nv_bfloat16*>(s.W1 + tc::kmajor_offset(o, kIn + i, kInHL)) = w->W1[idx];
-    }
-    for (int idx = threadIdx.x; idx < kHid * kHid; idx += blockDim.x)
-        *reinterpret_cast<__nv_bfloat16*>(s.W2 + tc::kmajor_offset(idx / kHid, idx % kHid, kHid)) = w->W2[idx];
-    for (int idx = threadIdx.x; idx < kOutP * kHid; idx += blockDim.x)
-        *reinterpret_cast<__nv_bfloat16*>(s.W3 + tc::kmajor_offset(idx / kHid, idx % kHid, kHid)) = w->W3[idx];
-    for (int idx = threadIdx.x; idx < kHid; idx += blockDim.x) {
-        s.b1[idx] = w->b1[idx];
-        s.b2[idx] = w->b2[idx];
-    }
-    for (int idx = threadIdx.x; idx < kOutP; idx += blockDim.x) s.b3[idx] = w->b3[idx];
-}
-
-// Row t of the layer-1 input tile: BF16 high parts, then low parts.
-__device__ __forceinline__ void store_input_row(unsigned char* X, int t, const float x[27]) {
-    for (int q = 0; q < kIn; ++q) {
-        __nv_bfloat16 hi, lo;
-        split_bf16(q < 27 ? x[q] : 0.f, hi, lo);
-        *reinterpret_cast<__nv_bfloat16*>(X + tc::kmajor_offset(t, q, kInHL)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(X + tc::kmajor_offset(t, kIn + q, kInHL)) = lo;
-    }
-}
-
-// Tensor-memory columns of the three layer outputs.
-// D3 reuses D1's columns (D1 is in registers before layer 2 is issued), so
-// four CTAs fit the 512 columns of an SM.
-constexpr uint32_t kColD1 = 0, kColD2 = 64, kColD3 = 0, kTmemCols = 128;
-
-// Issue one layer (thread 0): D = A * W^T over K in steps of 16.
-__device__ __forceinline__ void issue_layer(uint32_t d, const unsigned char* A, const unsigned char* W, int K, int N,
-                                            uint64_t* bar) {
-    const uint32_t idesc = tc::idesc_bf16(128, N);
-    for (int s = 0; s < K / 16; ++s)
-        tc::mma_bf16(d, tc::sdesc(tc::smem_u32(A) + s * 256, K), tc::sdesc(tc::smem_u32(W) + s * 256, K), idesc,
-                     s > 0);
-    tc::mma_commit(bar);
-}
-
-// Wait for the layer, bring its row into registers.  Returns false on a
-// timed-out wait (the caller stops and reports it).
-__device__ __forceinline__ bool finish_layer(MlpSmem& s, uint32_t& phase) {
-    const bool ok = tc::mbar_wait(&s.bar, phase & 1u);
-    phase += 1;
-    // every thread takes the same decision (no thread may stop at a
-    // different barrier than the others)
-    const int failed = __syncthreads_or(!ok);
-    tc::fence_after_sync();
-    if (failed) {
-        if (threadIdx.x == 0) s.timeout = 1;
-        return false;
-    }
-    return true;
-}
-
-// Forward pass of the tile whose canonical inputs are in s.X.  out[3] gets
-// this thread's canonical output.  Every thread of the CTA must call it.
-__device__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uint32_t& phase, float out[3]) {
-    const int t = threadIdx.x;
-    const uint32_t lane_off = (uint32_t)(32 * (t >> 5)) << 16;
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD1, s.X, s.W1, kInHL, kHid, &s.bar);
-    if (!finish_layer(s, phase)) return false;
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + lane_off + kColD1 + c0, v);
-        for (int q = 0; q < 16; ++q) tc::store_bf16(s.H, t, c0 + q, kHid, fmaxf(v[q] + s.b1[c0 + q], 0.f));
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD2, s.H, s.W2, kHid, kHid, &s.bar);
-    if (!finish_layer(s, phase)) return false;
-    float h2[kHid];
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + lane_off + kColD2 + c0, v);
-        for (int q = 0; q < 16; ++q) h2[c0 + q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
-    }
-    // layer 2 has finished reading H: reuse it for layer 3's input
-    for (int q = 0; q < kHid; ++q) tc::store_bf16(s.H, t, q, kHid, h2[q]);
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD3, s.H, s.W3, kHid, kOutP, &s.bar);
-    if (!finish_layer(s, phase)) return false;
-    float v[16];
-    tc::tmem_ld16(taddr + lane_off + kColD3, v);
-    out[0] = v[0] + s.b3[0];
-    out[1] = v[1] + s.b3[1];
-    out[2] = v[2] + s.b3[2];
-    return true;
-}
-
-__device__ void mlp_cta_begin(MlpSmem& s, const MlpBlob* w) {
-    load_weights(s, w);
-    if (threadIdx.x == 0) {
-        tc::mbar_init(&s.bar, 1);
-        s.timeout = 0;
-    }
-    if (threadIdx.x < 32) {
-        tc::tmem_alloc(&s.tbase, kTmemCols);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-}
-
-__device__ void mlp_cta_end(MlpSmem& s, int* status) {
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (threadIdx.x < 32) tc::tmem_dealloc(s.tbase, kTmemCols);
-    if (threadIdx.x == 0 && s.timeout && status) atomicExch(status, 1);
-}
-
 // Normal of each raw stencil st[n][27] (float): canonicalise, run the
 // network, map back, L2-normalise.  Output n_out[n][3].
 __global__ void __launch_bounds__(128, 4) k_mlp_forward(const MlpBlob* __restrict__ w, const float* __restrict__ st,
@@ -244,7 +105,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_forward(const MlpBlob* __restric
         canon_frame(sv, fr);
         float x[27];
         canon_input(sv, fr, x);
-        store_input_row(s.X, t, x);
+        store_input_row(s, t, x);
         float oc[3];
         if (!mlp_tile_forward(s, taddr, phase, oc)) break;
         float nn[3];
@@ -258,6 +119,53 @@ __global__ void __launch_bounds__(128, 4) k_mlp_forward(const MlpBlob* __restric
         }
     }
     mlp_cta_end(s, status);
+}
+
+// The judged learned normal of each raw stencil (the estimator exactly as
+// the learned step applies it to a donor): m_out[n][3] L1-normalised,
+// which_out[n] = 0 network kept, 1 MYC.
+__global__ void __launch_bounds__(128, 3) k_learned_normals(const MlpBlob* __restrict__ w,
+                                                            const float* __restrict__ st, float tol,
+                                                            float* __restrict__ m_out,
+                                                            int* __restrict__ which_out, long long n,
+                                                            int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
+    mlp_cta_begin(s, w);
+    const uint32_t taddr = s.tbase;
+    uint32_t phase = 0;
+    const int t = threadIdx.x;
+    for (long long base = (long long)blockIdx.x * 128; base < n; base += (long long)gridDim.x * 128) {
+        const long long r = base + t;
+        float sv[27];
+        for (int q = 0; q < 27; ++q) sv[q] = r < n ? st[r * 27 + q] : 0.5f;
+        CanonFrame fr;
+        canon_frame(sv, fr);
+        float x[27];
+        canon_input(sv, fr, x);
+        store_input_row(s, t, x);
+        float oc[3];
+        if (!mlp_tile_forward(s, taddr, phase, oc)) break;
+        if (r < n) {
+            float nn[3], m[3];
+            canon_output(oc, fr, nn);
+            const bool keep = judged_normal(sv, nn, tol, m);
+            m_out[r * 3 + 0] = m[0];
+            m_out[r * 3 + 1] = m[1];
+            m_out[r * 3 + 2] = m[2];
+            which_out[r] = keep ? 0 : 1;
+        }
+    }
+    mlp_cta_end(s, status);
+}
+
+cudaError_t learned_normals(const MlpBlob* w, const float* st, float tol, float* m_out, int* which_out,
+                            long long n, int* status, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    cudaFuncSetAttribute(k_learned_normals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+    const int blocks = (int)std::min<long long>((n + 127) / 128, 152LL * 3);
+    k_learned_normals<<<blocks, 128, sizeof(MlpSmem), stream>>>(w, st, tol, m_out, which_out, n, status);
+    return cudaGetLastError();
 }
 
 cudaError_t mlp_forward(const MlpBlob* w, const float* st, float* n_out, long long n, int* status,
@@ -301,6 +209,23 @@ extern "C" vof_status vof_mlp_forward(const void* weights_dev, const float* sten
     int* sp = status_ptr();
     if (!sp || cudaMemsetAsync(sp, 0, sizeof(int), st) != cudaSuccess) return VOF_ERR_CUDA;
     if (vof::mlp_forward((const vof::MlpBlob*)weights_dev, stencils_dev, normals_dev, n, sp, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return VOF_ERR_CUDA;
+    }
+    return read_status(st);
+}
+
+extern "C" vof_status vof_learned_normals(const void* weights_dev, const float* stencils_dev, int64_t n,
+                                          double fallback_tol, float* normals_dev, int32_t* which_dev,
+                                          void* stream) {
+    if (n < 0 || (n > 0 && (!weights_dev || !stencils_dev || !normals_dev || !which_dev)) ||
+        !(fallback_tol >= 0.0) || !std::isfinite(fallback_tol))
+        return VOF_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* sp = status_ptr();
+    if (!sp || cudaMemsetAsync(sp, 0, sizeof(int), st) != cudaSuccess) return VOF_ERR_CUDA;
+    if (vof::learned_normals((const vof::MlpBlob*)weights_dev, stencils_dev, (float)fallback_tol, normals_dev,
+                             which_dev, n, sp, st) != cudaSuccess) {
         (void)cudaGetLastError();
         return VOF_ERR_CUDA;
     }

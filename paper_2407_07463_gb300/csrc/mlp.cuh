@@ -5,12 +5,14 @@
 #include <stdint.h>
 
 #include "plic.cuh"
+#include "tc.cuh"
 
 namespace vof {
 
 constexpr int kIn = 32;     // 27 stencil values padded to 32
 constexpr int kInHL = 64;   // layer-1 K: BF16 high parts in 0..31, low parts in 32..63
 constexpr int kHid = 64;
+constexpr int kHidHL = 128; // layer-2/3 K: high parts in 0..63, low parts in 64..127
 constexpr int kOut = 3;
 constexpr int kOutP = 16;   // output rows padded to the smallest MMA N
 
@@ -67,29 +69,50 @@ __device__ __forceinline__ void canon_output(const float nc[3], const CanonFrame
     for (int q = 0; q < 3; ++q) n[fr.perm[q]] = (float)fr.sign[fr.perm[q]] * nc[q];
 }
 
-// BF16 split of an input: x ~ hi + lo with both parts representable.
+// BF16 split of a layer input: x ~ hi + lo with both parts representable
+// (about 16 significant bits; each weight multiplies both parts).
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Residual of a normal n on a stencil: plane through the centre cell with
-// the centre's volume fraction, extended into the six face neighbours; the
-// largest |predicted - actual| fraction.  (Judge of the learned normal.)
+// Store v as the pair (hi at column k, lo at column k + half) of row r of a
+// K-major tile with kext columns.
+__device__ __forceinline__ void store_pair(unsigned char* tile, int r, int k, int half, int kext, float v) {
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(r, k, kext)) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(r, k + half, kext)) = lo;
+}
+
+// Weight matrix w[rows][cols] (global, BF16) into a K-major tile holding it
+// twice along K: columns c and cols + c.
+__device__ __forceinline__ void load_weight_pair(unsigned char* tile, const __nv_bfloat16* __restrict__ w, int rows,
+                                                 int cols, int tid, int nthreads) {
+    for (int idx = tid; idx < rows * cols; idx += nthreads) {
+        const int o = idx / cols, i = idx % cols;
+        *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(o, i, 2 * cols)) = w[idx];
+        *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(o, cols + i, 2 * cols)) = w[idx];
+    }
+}
+
+// Residual of a normal n on a stencil (judge of the learned normal): the
+// plane of normal n holding the centre cell's volume fraction, extended over
+// the 3x3x3 block; the mean over the 27 cells of |predicted - actual|
+// fraction.  +inf for a zero or non-finite n.
 __device__ __forceinline__ float normal_residual(const float st[27], const float n[3]) {
     const float l1 = fabsf(n[0]) + fabsf(n[1]) + fabsf(n[2]);
     if (!(l1 > 0.f) || !isfinite(l1)) return INFINITY;
     const float m0 = n[0] / l1, m1 = n[1] / l1, m2 = n[2] / l1;
     const float al = plic_alpha<float>(m0, m1, m2, st[13]);
     float e = 0.f;
-    const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const float a = al - (m0 * off[q][0] + m1 * off[q][1] + m2 * off[q][2]);
-        const float v = plic_volume<float>(m0, m1, m2, a);
-        e = fmaxf(e, fabsf(v - VOF_ST(st, off[q][0], off[q][1], off[q][2])));
+#pragma unroll 1
+    for (int q = 0; q < 27; ++q) {
+        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
+        const float v = plic_volume<float>(m0, m1, m2, al - (m0 * i + m1 * j + m2 * k));
+        e += fabsf(v - st[q]);
     }
-    return e;
+    return e * (1.f / 27.f);
 }
 
 }  // namespace vof

@@ -1,0 +1,166 @@
+// One CTA-wide forward pass of the learned normal estimator over a tile of
+// 128 canonical stencils on the tensor cores (internal): weights staged in
+// shared memory, each layer one tcgen05 MMA chain (M = 128, BF16 operands,
+// FP32 accumulation in tensor memory) issued by one thread, bias + ReLU in
+// the epilogue of the thread that owns the row.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "mlp.cuh"
+#include "plic.cuh"
+#include "tc.cuh"
+
+namespace vof {
+
+// Shared-memory image of the network plus activation tiles.
+// H holds the layer-1 input (128 x 64, hi | lo) at its start, then each
+// hidden activation tile (128 x 128, hi | lo) once the layer reading the
+// previous content has completed.
+struct MlpSmem {
+    unsigned char H[128 * kHidHL * 2];     // 128 x 128
+    unsigned char W1[kHid * kInHL * 2];    // 64 x 64 (W1 | W1)
+    unsigned char W2[kHid * kHidHL * 2];   // 64 x 128 (W2 | W2)
+    unsigned char W3[kOutP * kHidHL * 2];  // 16 x 128 (W3 | W3)
+    float b1[kHid], b2[kHid], b3[kOutP];
+    uint64_t bar;
+    uint32_t tbase;
+    int timeout;
+};
+
+__device__ __forceinline__ void load_weights(MlpSmem& s, const MlpBlob* __restrict__ w) {
+    load_weight_pair(s.W1, w->W1, kHid, kIn, threadIdx.x, blockDim.x);
+    load_weight_pair(s.W2, w->W2, kHid, kHid, threadIdx.x, blockDim.x);
+    load_weight_pair(s.W3, w->W3, kOutP, kHid, threadIdx.x, blockDim.x);
+    for (int idx = threadIdx.x; idx < kHid; idx += blockDim.x) {
+        s.b1[idx] = w->b1[idx];
+        s.b2[idx] = w->b2[idx];
+    }
+    for (int idx = threadIdx.x; idx < kOutP; idx += blockDim.x) s.b3[idx] = w->b3[idx];
+}
+
+// Row t of the layer-1 input tile: BF16 high parts, then low parts.
+__device__ __forceinline__ void store_input_row(MlpSmem& s, int t, const float x[27]) {
+    for (int q = 0; q < kIn; ++q) store_pair(s.H, t, q, kIn, kInHL, q < 27 ? x[q] : 0.f);
+}
+
+// Tensor-memory columns of the three layer outputs.
+// D3 reuses D1's columns (D1 is in shared memory before layer 2 is issued),
+// so four CTAs would fit the 512 columns of an SM.
+constexpr uint32_t kColD1 = 0, kColD2 = 64, kColD3 = 0, kTmemCols = 128;
+
+// Issue one layer (thread 0): D = A * W^T over K in steps of 16.
+__device__ __forceinline__ void issue_layer(uint32_t d, const unsigned char* A, const unsigned char* W, int K, int N,
+                                            uint64_t* bar) {
+    const uint32_t idesc = tc::idesc_bf16(128, N);
+    for (int s = 0; s < K / 16; ++s)
+        tc::mma_bf16(d, tc::sdesc(tc::smem_u32(A) + s * 256, K), tc::sdesc(tc::smem_u32(W) + s * 256, K), idesc,
+                     s > 0);
+    tc::mma_commit(bar);
+}
+
+// Wait for the layer, bring its row into registers.  Returns false on a
+// timed-out wait (the caller stops and reports it).
+__device__ __forceinline__ bool finish_layer(MlpSmem& s, uint32_t& phase) {
+    const bool ok = tc::mbar_wait(&s.bar, phase & 1u);
+    phase += 1;
+    // every thread takes the same decision (no thread may stop at a
+    // different barrier than the others)
+    const int failed = __syncthreads_or(!ok);
+    tc::fence_after_sync();
+    if (failed) {
+        if (threadIdx.x == 0) s.timeout = 1;
+        return false;
+    }
+    return true;
+}
+
+// Forward pass of the tile whose canonical inputs are in s.H.  out[3] gets
+// this thread's canonical output.  Every thread of the CTA must call it.
+__device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uint32_t& phase, float out[3]) {
+    const int t = threadIdx.x;
+    const uint32_t lane_off = (uint32_t)(32 * (t >> 5)) << 16;
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) issue_layer(taddr + kColD1, s.H, s.W1, kInHL, kHid, &s.bar);
+    if (!finish_layer(s, phase)) return false;
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + lane_off + kColD1 + c0, v);
+        for (int q = 0; q < 16; ++q) store_pair(s.H, t, c0 + q, kHid, kHidHL, fmaxf(v[q] + s.b1[c0 + q], 0.f));
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) issue_layer(taddr + kColD2, s.H, s.W2, kHidHL, kHid, &s.bar);
+    if (!finish_layer(s, phase)) return false;
+    float h2[kHid];
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + lane_off + kColD2 + c0, v);
+        for (int q = 0; q < 16; ++q) h2[c0 + q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
+    }
+    // layer 2 has finished reading H: reuse it for layer 3's input
+    for (int q = 0; q < kHid; ++q) store_pair(s.H, t, q, kHid, kHidHL, h2[q]);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) issue_layer(taddr + kColD3, s.H, s.W3, kHidHL, kOutP, &s.bar);
+    if (!finish_layer(s, phase)) return false;
+    float v[16];
+    tc::tmem_ld16(taddr + lane_off + kColD3, v);
+    out[0] = v[0] + s.b3[0];
+    out[1] = v[1] + s.b3[1];
+    out[2] = v[2] + s.b3[2];
+    return true;
+}
+
+__device__ __forceinline__ void mlp_cta_begin(MlpSmem& s, const MlpBlob* w) {
+    load_weights(s, w);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s.bar, 1);
+        s.timeout = 0;
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&s.tbase, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ void mlp_cta_end(MlpSmem& s, int* status) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(s.tbase, kTmemCols);
+    if (threadIdx.x == 0 && s.timeout && status) atomicExch(status, 1);
+}
+
+// The learned normal as the step uses it: the network's normal nn (original
+// frame) is kept when the mean residual of its plane over the stencil is at
+// most tol, or no larger than that of MYC's normal; otherwise MYC's.  m gets
+// the L1-normalised choice; returns true when the network's was kept.
+__device__ __forceinline__ bool judged_normal(const float st[27], const float nn[3], float tol, float m[3]) {
+    const float e_net = normal_residual(st, nn);
+    bool keep = e_net <= tol;
+    if (!keep) {
+        myc_normal(st, m);
+        keep = e_net <= normal_residual(st, m);
+    }
+    if (keep) {
+        const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
+        m[0] = nn[0] * inv;
+        m[1] = nn[1] * inv;
+        m[2] = nn[2] * inv;
+    }
+    return keep;
+}
+
+}  // namespace vof

@@ -3,12 +3,16 @@
 // forward and backward passes on the tensor cores (tcgen05, BF16 operands,
 // FP32 accumulation in tensor memory), Adam on FP32 master weights.
 //
+// Every layer input (stencil, H1, H2) enters the forward pass as the BF16
+// pair (hi, lo) against the weights held twice along K, as in inference.
 // Backward of a tile of 128 samples (thread b owns sample b):
 //   dY3 = d loss / d out                      (registers)
 //   dH2 = dY3 W3,   dA2 = dH2 [a2 > 0]        (MMA, A = dY3, B = W3^T)
 //   dH1 = dA2 W2,   dA1 = dH1 [a1 > 0]        (MMA, A = dA2, B = W2^T)
 //   dW3^T += H2^T dY3, dW2^T += H1^T dA2, dW1^T += X^T dA1
-//                                             (MMA, K = the 128 samples)
+//                                             (MMA, K = the 128 samples; the
+//                                              hi and lo rows are summed on
+//                                              the way out)
 // The weight gradients accumulate in tensor memory over a CTA's tiles and
 // are added to the global FP32 gradient once per launch.
 #include <cuda_bf16.h>
@@ -134,15 +138,15 @@ __global__ void k_mlp_gen(float* __restrict__ st, float* __restrict__ tgt, long 
 // forward + backward of tiles of 128 samples
 
 struct TrainSmem {
-    unsigned char W1[kHid * kInHL * 2];   // 64 x 64 (B of layer 1: W1 | W1)
-    unsigned char W2[kHid * kHid * 2];    // 64 x 64
-    unsigned char W3[kOutP * kHid * 2];   // 16 x 64
-    unsigned char W2T[kHid * kHid * 2];   // 64 x 64: W2^T (B of dH1 = dA2 W2)
-    unsigned char W3T[kHid * kOutP * 2];  // 64 x 16: W3^T (B of dH2 = dY3 W3)
-    unsigned char X[128 * kInHL * 2];     // 128 x 64 (hi | lo)
-    unsigned char H1[128 * kHid * 2];     // 128 x 64
-    unsigned char H2[128 * kHid * 2];     // 128 x 64
-    unsigned char T[128 * 128 * 2];       // 128 x 128: [hi|lo]^T, H1^T or H2^T (rows = features)
+    unsigned char W1[kHid * kInHL * 2];    // 64 x 64 (B of layer 1: W1 | W1)
+    unsigned char W2[kHid * kHidHL * 2];   // 64 x 128 (W2 | W2)
+    unsigned char W3[kOutP * kHidHL * 2];  // 16 x 128 (W3 | W3)
+    unsigned char W2T[kHid * kHid * 2];    // 64 x 64: W2^T (B of dH1 = dA2 W2)
+    unsigned char W3T[kHid * kOutP * 2];   // 64 x 16: W3^T (B of dH2 = dY3 W3)
+    unsigned char X[128 * kInHL * 2];      // 128 x 64 (hi | lo)
+    unsigned char H1[128 * kHidHL * 2];    // 128 x 128 (hi | lo)
+    unsigned char H2[128 * kHidHL * 2];    // 128 x 128 (hi | lo)
+    unsigned char T[128 * 128 * 2];        // 128 x 128: X^T, H1^T or H2^T (rows = hi/lo features)
     unsigned char DY[128 * kOutP * 2];    // 128 x 16: dY3
     unsigned char DYT[kOutP * 128 * 2];   // 16 x 128: dY3^T
     unsigned char DA[128 * kHid * 2];     // 128 x 64: dA2
@@ -198,19 +202,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
     TrainSmem& s = *reinterpret_cast<TrainSmem*>(smem_raw);
     const int t = threadIdx.x;
     // weights (forward and transposed copies), zeroed scratch
-    for (int idx = t; idx < kHid * kIn; idx += 128) {
-        const int o = idx / kIn, i = idx % kIn;
-        *reinterpret_cast<__nv_bfloat16*>(s.W1 + tc::kmajor_offset(o, i, kInHL)) = w->W1[idx];
-        *reinterpret_cast<__nv_bfloat16*>(s.W1 + tc::kmajor_offset(o, kIn + i, kInHL)) = w->W1[idx];
-    }
+    load_weight_pair(s.W1, w->W1, kHid, kIn, t, 128);
+    load_weight_pair(s.W2, w->W2, kHid, kHid, t, 128);
+    load_weight_pair(s.W3, w->W3, kOutP, kHid, t, 128);
     for (int idx = t; idx < kHid * kHid; idx += 128) {
         const int o = idx / kHid, i = idx % kHid;
-        *reinterpret_cast<__nv_bfloat16*>(s.W2 + tc::kmajor_offset(o, i, kHid)) = w->W2[idx];
         *reinterpret_cast<__nv_bfloat16*>(s.W2T + tc::kmajor_offset(i, o, kHid)) = w->W2[idx];
     }
     for (int idx = t; idx < kOutP * kHid; idx += 128) {
         const int o = idx / kHid, i = idx % kHid;
-        *reinterpret_cast<__nv_bfloat16*>(s.W3 + tc::kmajor_offset(o, i, kHid)) = w->W3[idx];
         *reinterpret_cast<__nv_bfloat16*>(s.W3T + tc::kmajor_offset(i, o, kOutP)) = w->W3[idx];
     }
     for (int idx = t; idx < kHid; idx += 128) {
@@ -259,12 +259,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
         float x[27], tc3[3];
         canon_input(sv, fr, x);
         for (int q = 0; q < 3; ++q) tc3[q] = (float)fr.sign[fr.perm[q]] * tr[fr.perm[q]];
-        for (int q = 0; q < kIn; ++q) {
-            __nv_bfloat16 hi, lo;
-            split_bf16((q < 27 && valid) ? x[q] : 0.f, hi, lo);
-            *reinterpret_cast<__nv_bfloat16*>(s.X + tc::kmajor_offset(t, q, kInHL)) = hi;
-            *reinterpret_cast<__nv_bfloat16*>(s.X + tc::kmajor_offset(t, kIn + q, kInHL)) = lo;
-        }
+        for (int q = 0; q < kIn; ++q) store_pair(s.X, t, q, kIn, kInHL, (q < 27 && valid) ? x[q] : 0.f);
         // ---- forward
         publish_smem();
         if (t == 0) chain(tm + kTD1, s.X, kInHL, s.W1, kInHL, kInHL, kHid, false);
@@ -272,18 +267,18 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
         for (int c0 = 0; c0 < kHid; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tm + lane + kTD1 + c0, v);
-            for (int q = 0; q < 16; ++q) tc::store_bf16(s.H1, t, c0 + q, kHid, fmaxf(v[q] + s.b1[c0 + q], 0.f));
+            for (int q = 0; q < 16; ++q) store_pair(s.H1, t, c0 + q, kHid, kHidHL, fmaxf(v[q] + s.b1[c0 + q], 0.f));
         }
         publish_smem();
-        if (t == 0) chain(tm + kTD2, s.H1, kHid, s.W2, kHid, kHid, kHid, false);
+        if (t == 0) chain(tm + kTD2, s.H1, kHidHL, s.W2, kHidHL, kHidHL, kHid, false);
         if (!(alive = commit_wait(s, phase))) break;
         for (int c0 = 0; c0 < kHid; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tm + lane + kTD2 + c0, v);
-            for (int q = 0; q < 16; ++q) tc::store_bf16(s.H2, t, c0 + q, kHid, fmaxf(v[q] + s.b2[c0 + q], 0.f));
+            for (int q = 0; q < 16; ++q) store_pair(s.H2, t, c0 + q, kHid, kHidHL, fmaxf(v[q] + s.b2[c0 + q], 0.f));
         }
         publish_smem();
-        if (t == 0) chain(tm + kTD3, s.H2, kHid, s.W3, kHid, kHid, kOutP, false);
+        if (t == 0) chain(tm + kTD3, s.H2, kHidHL, s.W3, kHidHL, kHidHL, kOutP, false);
         if (!(alive = commit_wait(s, phase))) break;
         float out[3];
         {
@@ -307,7 +302,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
             if (q < 3) tc::store_bf16(s.DYT, q, t, 128, v);
         }
         for (int q = 0; q < 3; ++q) atomicAdd(&s.gb3[q], dy[q]);
-        for (int i = 0; i < kHid; ++i) tc::store_bf16(s.T, i, t, 128, bf(s.H2, t, i, kHid));  // H2^T
+        for (int i = 0; i < kHidHL; ++i) tc::store_bf16(s.T, i, t, 128, bf(s.H2, t, i, kHidHL));  // H2^T
         // ---- dH2 = dY3 W3 ; dW3^T += H2^T dY3
         publish_smem();
         if (t == 0) {
@@ -320,13 +315,13 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
             tc::tmem_ld16(tm + lane + kTdH2 + c0, v);
             for (int q = 0; q < 16; ++q) {
                 const int i = c0 + q;
-                const float da = bf(s.H2, t, i, kHid) > 0.f ? v[q] : 0.f;
+                const float da = bf(s.H2, t, i, kHidHL) > 0.f ? v[q] : 0.f;
                 tc::store_bf16(s.DA, t, i, kHid, da);
                 tc::store_bf16(s.DAT, i, t, 128, da);
                 atomicAdd(&s.gb2[i], da);
             }
         }
-        for (int i = 0; i < kHid; ++i) tc::store_bf16(s.T, i, t, 128, bf(s.H1, t, i, kHid));  // H1^T
+        for (int i = 0; i < kHidHL; ++i) tc::store_bf16(s.T, i, t, 128, bf(s.H1, t, i, kHidHL));  // H1^T
         // ---- dH1 = dA2 W2 ; dW2^T += H1^T dA2
         publish_smem();
         if (t == 0) {
@@ -339,7 +334,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
             tc::tmem_ld16(tm + lane + kTdH1 + c0, v);
             for (int q = 0; q < 16; ++q) {
                 const int i = c0 + q;
-                const float da = bf(s.H1, t, i, kHid) > 0.f ? v[q] : 0.f;
+                const float da = bf(s.H1, t, i, kHidHL) > 0.f ? v[q] : 0.f;
                 tc::store_bf16(s.DAT, i, t, 128, da);
                 atomicAdd(&s.gb1[i], da);
             }
@@ -354,13 +349,12 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
     // ---- gradients of this CTA to global memory
     if (alive && !first) {
         float v[16];
-        tc::tmem_ld16(tm + lane + kTgW3, v);  // row t = input i of W3, columns o
-        if (t < kHid)
-            for (int o = 0; o < 3; ++o) atomicAdd(&grad[kOffW3 + o * kHid + t], v[o]);
+        // row t = hi (t < 64) or lo (t >= 64) part of input t mod 64 of W3 / W2
+        tc::tmem_ld16(tm + lane + kTgW3, v);
+        for (int o = 0; o < 3; ++o) atomicAdd(&grad[kOffW3 + o * kHid + (t & 63)], v[o]);
         for (int c0 = 0; c0 < kHid; c0 += 16) {
             tc::tmem_ld16(tm + lane + kTgW2 + c0, v);
-            if (t < kHid)
-                for (int q = 0; q < 16; ++q) atomicAdd(&grad[kOffW2 + (c0 + q) * kHid + t], v[q]);
+            for (int q = 0; q < 16; ++q) atomicAdd(&grad[kOffW2 + (c0 + q) * kHid + (t & 63)], v[q]);
             // rows 0..31 (high parts) and 32..63 (low parts) both feed W1[o][row mod 32]
             tc::tmem_ld16(tm + lane + kTgW1 + c0, v);
             if ((t & 31) < 27 && t < kInHL)

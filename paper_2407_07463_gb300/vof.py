@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvof.so")
 
 VOF_OK = 0
-VOF_ERR_NO_FREE_FIELD = -4
+VOF_ERR_ARG, VOF_ERR_CUDA, VOF_ERR_WORKSPACE, VOF_ERR_NO_FREE_FIELD = -1, -2, -3, -4
+VOF_ERR_CFL, VOF_ERR_TIMEOUT, VOF_ERR_STATE, VOF_ERR_NONFINITE, VOF_ERR_CAPACITY = -5, -6, -7, -8, -9
 VOF_FP64, VOF_MIXED, VOF_MIXED_LEARNED = 0, 1, 2
 
 STATUS = {0: "VOF_OK", -1: "VOF_ERR_ARG", -2: "VOF_ERR_CUDA", -3: "VOF_ERR_WORKSPACE",
@@ -41,7 +42,8 @@ class vof_config(C.Structure):
 class vof_step_report(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("clipped_volume", C.c_double),
                 ("n_active", C.c_int32), ("n_moved", C.c_int32),
-                ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64)]
+                ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64),
+                ("faces_network", C.c_int64), ("faces_myc", C.c_int64)]
 
 
 class vof_train_params(C.Structure):
@@ -74,7 +76,7 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_profile_class_name", "vof_label_noalloc", "vof_mlp_weights_size",
            "vof_mlp_forward", "vof_tc_gemm_check", "vof_mlp_train_params_default",
            "vof_mlp_train_workspace_size", "vof_mlp_train", "vof_mlp_grad",
-           "vof_mlp_params_to_weights"]
+           "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals"]
 
 
 def lib():
@@ -121,6 +123,8 @@ def lib():
                                     C.POINTER(vof_train_report)]),
         "vof_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "vof_mlp_params_to_weights": (C.c_int, [vp, vp, vp]),
+        "vof_set_mlp": (C.c_int, [vp, vp, dbl]),
+        "vof_learned_normals": (C.c_int, [vp, vp, i64, dbl, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -270,6 +274,18 @@ def vof_mlp_train(tp, device="cuda", stream=None):
     return w, {k: getattr(rep, k) for k, _ in vof_train_report._fields_}
 
 
+def vof_learned_normals(weights, stencils, fallback_tol=1e-3, stream=None):
+    """Judged learned normals of float stencils [n][27] (device); returns
+    (normals [n][3] float, which [n] int32: 0 network, 1 MYC)."""
+    import torch
+    n = stencils.shape[0]
+    m = torch.empty((n, 3), dtype=torch.float32, device=stencils.device)
+    which = torch.empty(n, dtype=torch.int32, device=stencils.device)
+    _check(lib().vof_learned_normals(_ptr(weights), _ptr(stencils), n, float(fallback_tol), _ptr(m),
+                                     _ptr(which), _stream(stream)), "vof_learned_normals")
+    return m, which
+
+
 def vof_tc_gemm_check(a, b, variant=0, stream=None):
     import torch
     n, k = b.shape
@@ -327,9 +343,16 @@ class Context:
             return None
         return {"status": st, "steps_done": rep.steps_done, "clipped_volume": rep.clipped_volume,
                 "n_active": rep.n_active, "n_moved": rep.n_moved,
-                "near_contact_steps": rep.near_contact_steps, "field_steps": rep.field_steps}
+                "near_contact_steps": rep.near_contact_steps, "field_steps": rep.field_steps,
+                "faces_network": rep.faces_network, "faces_myc": rep.faces_myc}
 
     step = vof_step
+
+    def vof_set_mlp(self, weights, fallback_tol=1e-3):
+        """Borrow a device weight blob (uint8 tensor of vof_mlp_weights_size()
+        bytes) for the learned normal; it must outlive its use."""
+        self.mlp_weights = weights
+        _check(lib().vof_set_mlp(self.handle, _ptr(weights), float(fallback_tol)), "vof_set_mlp")
 
     def vof_set_velocity(self, u):
         self.u = u

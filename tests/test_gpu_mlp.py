@@ -115,3 +115,37 @@ def test_training_gains_over_myc(vof):
     assert rep["test_p95_deg_mlp"] < rep["test_p95_deg_myc"]
     assert rep["test_mean_deg_combined"] < rep["test_mean_deg_myc"]
     assert rep["test_p95_deg_combined"] < rep["test_p95_deg_myc"]
+
+
+@pytest.mark.parametrize("radius", [4.0, 8.0])
+def test_translated_sphere_shape_error(vof, radius):
+    """A sphere carried by a uniform oblique velocity for 16 cells along z:
+    L1 distance to the exact translated sphere with the trained network
+    (MYC fallback) and with MYC alone, same FP32 step otherwise."""
+    from paper_2407_07463_gb300 import synth
+    tp = vof.train_params(n_train=4_000_000, n_test=10_000, epochs=4, batch=16384, seed=7)
+    wts, _ = vof.vof_mlp_train(tp, DEV)
+    shape = (48, 40, 40)
+    c0 = np.array([[15.3, 16.7, 12.4]])
+    vel = np.array([0.3, 0.2, 1.0])
+    u = synth.uniform_velocity(shape, vel)
+    dt, steps = 0.25, 64
+    c = synth.sphere_cell_fractions(shape, c0, radius)[None]
+    exact = synth.sphere_cell_fractions(shape, c0 + vel * dt * steps, radius)
+    errs = {}
+    for prec in (1, 2):
+        cfg = vof.make_config(shape[2], shape[1], shape[0], k_capacity=1, k_active=1, precision=prec,
+                              tag_tau=0.0)
+        c_d = torch.from_numpy(c).to(DEV, torch.float32).contiguous()
+        u_d = torch.from_numpy(u).to(DEV, torch.float32).contiguous()
+        ctx = vof.Context(cfg, c_d, u_d)
+        if prec == 2:
+            ctx.vof_set_mlp(wts, 1e-3)
+        rep = ctx.vof_step(dt, steps)
+        torch.cuda.synchronize()
+        errs[prec] = float(np.abs(c_d.cpu().numpy()[0].astype(np.float64) - exact).sum())
+        if prec == 2:
+            errs["share"] = rep["faces_network"] / max(1, rep["faces_network"] + rep["faces_myc"])
+        ctx.close()
+    print("radius", radius, "L1 MYC", errs[1], "L1 learned", errs[2], "network share", errs["share"])
+    assert errs[2] <= 1.1 * errs[1]
