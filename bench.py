@@ -7,7 +7,9 @@ test on every field, tagging and recolouring when it fires).  The workload is
 256^3 cells, K = 8 colour fields, phi = 0.3 (2347 spheres of radius 8 cells,
 coloured greedily over the fields), a 16-mode solenoidal velocity with
 amplitude 0.5 plus a vertical drift of 1, CFL 0.3.  Metric: cell-field updates
-per second = cells x active fields x steps / time.
+per second = cells x active fields x steps / time.  The headline path is FP32
+with the learned normal (network trained on the GPU before the timed region,
+MYC fallback); the plain FP64 path runs on the same workload for the ratio.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -47,7 +49,9 @@ def parse():
     p.add_argument("--n", type=int, default=256, help="cells per axis")
     p.add_argument("--k", type=int, default=8, help="colour fields")
     p.add_argument("--phi", type=float, default=0.3)
-    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--precision", choices=["learned", "mixed", "fp64"], default="learned")
+    p.add_argument("--train-samples", type=int, default=10_000_000)
+    p.add_argument("--train-epochs", type=int, default=4)
     p.add_argument("--fp64-steps", type=int, default=3, help="steps of the FP64 comparison run")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -149,19 +153,16 @@ def peaks():
 
 
 def algorithmic_bytes(cls, n_cells, fields, es):
-    """Minimum DRAM bytes one launch of a kernel class must move (per launch).
-    fused_step (a whole step of every active field): read c once, write c
-    once and one occupancy bit per cell-field, read the three velocity
-    components once.  update: read c_in, read c at the step start (c_c), write c_out per
-    cell-field, plus the sweep's velocity component per cell.
-    find_faces: read c_in per cell-field plus the velocity component.
-    pack_bits: read c per cell-field, write one bit.  near_contact: read and
-    write one bit per cell-field."""
-    if cls == "fused_step":
-        return n_cells * fields * (2 * es + 1 / 8) + 3 * n_cells * es
+    """Minimum DRAM bytes one launch of a kernel class must move.
+    update (one sweep of every active field): read c_in and write c_out per
+    cell-field, one c_c bit read or written and (last sweep) one occupancy
+    bit per cell-field, the sweep's and the next sweep's velocity component
+    per cell.  list_faces: read c per cell-field plus one velocity
+    component.  pack_bits: read c per cell-field, write one bit.
+    near_contact: read and write one bit per cell-field."""
     if cls == "update":
-        return n_cells * fields * 3 * es + n_cells * es
-    if cls == "find_faces":
+        return n_cells * fields * (2 * es + 2 / 8) + 2 * n_cells * es
+    if cls == "list_faces":
         return n_cells * fields * es + n_cells * es
     if cls == "pack_bits":
         return n_cells * fields * (es + 1 / 8)
@@ -170,18 +171,52 @@ def algorithmic_bytes(cls, n_cells, fields, es):
     return None
 
 
-def cpu_sample_rate(wl, edge, steps=1):
+def step_bytes(n_cells, fields, es):
+    """The method's own minimum per step (read and write c once per step,
+    the three velocity components once)."""
+    return n_cells * fields * 2 * es + 3 * n_cells * es
+
+
+def train_network(vof, torch, dev, args):
+    """Network of the learned normal, trained on the GPU (untimed)."""
+    tp = vof.train_params(n_train=args.train_samples, n_test=200_000, epochs=args.train_epochs,
+                          batch=16384, seed=12345)
+    t0 = time.perf_counter()
+    w, rep = vof.vof_mlp_train(tp, dev)
+    torch.cuda.synchronize()
+    rep["seconds"] = time.perf_counter() - t0
+    return w, rep
+
+
+def host_network(seed=12345):
+    """He-initialised weights of the same architecture for the oracle's
+    timing sample (the oracle evaluates both estimators and both residuals on
+    every donor, so its cost does not depend on the weights)."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(7312)
+    p[0:2048].reshape(64, 32)[:, :27] = rng.normal(scale=math.sqrt(2 / 27), size=(64, 27))
+    p[2048:6144] = rng.normal(scale=math.sqrt(2 / 64), size=4096)
+    p[6144:7168].reshape(16, 64)[:3] = rng.normal(scale=math.sqrt(1 / 64), size=(3, 64))
+    return p
+
+
+def cpu_sample_rate(wl, edge, steps=1, learned=True):
     """Oracle (single thread) on the sub-box [0, edge)^3 of the workload:
-    one advection step of every active field, then Steps 1-4."""
+    one advection step of every active field (learned normal with MYC
+    fallback, or MYC alone), then Steps 1-4."""
     import oracle
 
     sub = np.ascontiguousarray(wl.c[:wl.k_active, :edge, :edge, :edge])
     u = np.ascontiguousarray(wl.u[:, :edge, :edge, :edge])
+    params = host_network()
     t0 = time.perf_counter()
     c = sub
     na = wl.k_active
     for s in range(steps):
-        c, _ = oracle.advect_step(c, u, wl.dt, wl.h, s)
+        if learned:
+            c, _, _ = oracle.advect_step_learned(c, u, wl.dt, wl.h, s, params, tol=1e-3)
+        else:
+            c, _ = oracle.advect_step(c, u, wl.dt, wl.h, s)
         full = np.zeros((wl.k_capacity,) + c.shape[1:])
         full[:na] = c[:na]
         full, na, _, _, _ = oracle.recolour(full, na, w=2)
@@ -217,10 +252,12 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": workload_desc(wl),
-                       "sample": f"oracle step (advect + Steps 1-4) on the {edge}^3 sub-box"},
+                       "sample": f"oracle step (learned-normal advection + Steps 1-4) on the "
+                                 f"{edge}^3 sub-box"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{edge}^3 x {wl.k_active} fields sub-box of the workload, "
-                                       f"one step per timed step"},
+                                       f"one step per timed step (learned normal, He-initialised "
+                                       f"weights, MYC fallback, Steps 1-4)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -254,15 +291,21 @@ def run_ours(args, rank, world):
     wl = workload(args.n, args.k, args.phi, seed=3 + rank)
     nz, ny, nx = wl.shape
     N = nx * ny * nz
-    prec = vof.VOF_MIXED if args.precision == "mixed" else vof.VOF_FP64
-    tdt = torch.float32 if prec == vof.VOF_MIXED else torch.float64
-    es = 4 if prec == vof.VOF_MIXED else 8
+    prec = {"learned": vof.VOF_MIXED_LEARNED, "mixed": vof.VOF_MIXED, "fp64": vof.VOF_FP64}[args.precision]
+    tdt = torch.float64 if prec == vof.VOF_FP64 else torch.float32
+    es = 8 if prec == vof.VOF_FP64 else 4
+    train = None
+    wts = None
+    if prec == vof.VOF_MIXED_LEARNED:
+        wts, train = train_network(vof, torch, dev, args)
     rbins = 2000
     cfg = vof.make_config(nx, ny, nz, k_capacity=wl.k_capacity, k_active=wl.k_active, precision=prec,
                           recolour=1, stats_rbins=rbins, stats_dr=0.16)
     c_d = torch.from_numpy(wl.c).to(dev, tdt).contiguous()
     u_d = torch.from_numpy(wl.u).to(dev, tdt).contiguous()
     ctx = vof.Context(cfg, c_d, u_d)
+    if wts is not None:
+        ctx.vof_set_mlp(wts, 1e-3)
     torch.cuda.synchronize()
     if args.warmup:
         ctx.vof_step(wl.dt, args.warmup)
@@ -323,7 +366,7 @@ def run_ours(args, rank, world):
 
     # FP64 comparison path on the same workload (plain FP64 kernels)
     fp64 = None
-    if not args.no_fp64 and prec == vof.VOF_MIXED and args.fp64_steps > 0:
+    if not args.no_fp64 and prec != vof.VOF_FP64 and args.fp64_steps > 0:
         del ctx
         torch.cuda.empty_cache()
         cfg64 = vof.make_config(nx, ny, nz, k_capacity=wl.k_capacity, k_active=wl.k_active,
@@ -373,19 +416,26 @@ def run_ours(args, rank, world):
         import oracle
 
         oracle.build()
-        r, t, u = cpu_sample_rate(wl, min(args.cpu_sample, args.n))
+        edge = min(args.cpu_sample, args.n)
+        r, t, u = cpu_sample_rate(wl, edge, learned=prec == vof.VOF_MIXED_LEARNED)
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle step (advect + Steps 1-4) of the {min(args.cpu_sample, args.n)}^3 "
-                         f"sub-box, {wl.k_active} active fields ({t:.1f} s)"}
+               "sample": f"one oracle step ({'learned-normal' if prec == vof.VOF_MIXED_LEARNED else 'MYC'} "
+                         f"advection + Steps 1-4) of the {edge}^3 sub-box, {wl.k_active} active fields "
+                         f"({t:.1f} s)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if prec == vof.VOF_MIXED else "f64", "data": "synthetic",
+            "dtype": "f64" if prec == vof.VOF_FP64 else "f32", "data": "synthetic",
             "config": {"workload": workload_desc(wl),
-                       "precision": "mixed (f32, f64 alpha band 1e-3 and clip sums)"
-                       if prec == vof.VOF_MIXED else "fp64",
-                       "normals": "MYC", "l2": "inputs larger than L2 (fields "
+                       "precision": "fp64" if prec == vof.VOF_FP64 else
+                       "mixed (f32, f64 alpha band 1e-3 and clip sums)",
+                       "normals": "learned (MLP 27-64-64-3, BF16 tcgen05, MYC fallback tol 1e-3)"
+                       if prec == vof.VOF_MIXED_LEARNED else "MYC",
+                       "faces_network": rep.get("faces_network"), "faces_myc": rep.get("faces_myc"),
+                       "training": train,
+                       "step_bytes_min": step_bytes(N, rep["field_steps"] / max(args.steps, 1), es),
+                       "l2": "inputs larger than L2 (fields "
                        f"{wl.k_capacity * N * es / 1e6:.0f} MB)",
                        "parallelism": f"{world} independent boxes" if world > 1 else "1 box",
                        "n_active_end": rep["n_active"], "drops_moved": rep["n_moved"],
@@ -394,7 +444,9 @@ def run_ours(args, rank, world):
             "cpu_baseline": cpu, "fp64_path": fp64,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
     if fp64:
-        line["mixed_over_fp64"] = value / world / fp64["value"]
+        line["over_fp64"] = value / world / fp64["value"]
+    line["step_roofline_frac"] = (step_bytes(N, rep["field_steps"] / max(args.steps, 1), es) /
+                                  (ms_max / args.steps * 1e-3) / 1e9 / hbm)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

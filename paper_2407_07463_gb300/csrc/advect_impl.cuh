@@ -56,6 +56,9 @@ struct AdvectArgs {
     Prof* prof;
     // learned normal (FP32 path only; null = MYC everywhere)
     const MlpBlob* mlp;
+    float4* net;                         // [K][N] network normal of each listed face's cell
+    int* tile_seg;                       // first segment of each tile of kFaceTile listed faces
+    int tile_cap;
     float mlp_tol;                       // residual below which the network is kept outright
     int* mlp_status;                     // set on a timed-out tensor-core wait
     unsigned long long* mlp_counters;    // [0] faces on the network's normal, [1] on MYC's
@@ -166,30 +169,59 @@ __device__ __forceinline__ int segment_of(const int* __restrict__ off, int nseg,
     return lo;
 }
 
+// Segment of entry e >= base given the segment sb of base: a short forward
+// walk (a tile of consecutive entries spans few segments).
+__device__ __forceinline__ int segment_from(const int* __restrict__ off, int sb, int e) {
+    while (off[sb + 1] <= e) ++sb;
+    return sb;
+}
+
+// Decoded listed face: field f, cell x of the face's high side, the cell
+// index t = f * N + x of its flux, the upwind donor cell.
+struct ListedFace {
+    int f, x, donor;
+    size_t t;
+};
+
+// uv receives the face velocity ud[x]; the donor is upwind of the face.
 template <typename T>
-__global__ void __launch_bounds__(128) k_face_flux(const T* __restrict__ cin, const T* __restrict__ ud,
-                                                   Dims g, int d, T sfac, T band,
-                                                   const unsigned long long* __restrict__ list, long long cap,
-                                                   const int* __restrict__ off, int nseg, T* __restrict__ flux) {
+__device__ __forceinline__ ListedFace decode_face(unsigned long long key, const Dims& g, int d,
+                                                  const T* __restrict__ ud, T& uv) {
+    ListedFace r;
+    r.f = (int)(key >> 54);
+    const int k = (int)((key >> 36) & 0x3ffffu);
+    const int j = (int)((key >> 18) & 0x3ffffu);
+    const int i = (int)(key & 0x3ffffu);
+    r.x = cell(i, j, k, g);
+    r.t = (size_t)r.f * g.N + r.x;
+    uv = ud[r.x];
+    r.donor = vsign(uv) > 0 ? step_cell(r.x, i, j, k, d, -1, g) : r.x;
+    return r;
+}
+
+// One thread per listed face, CTA-contiguous tiles of kFaceTile faces
+// (tile_seg gives each tile's first segment): MYC normal, plane constant
+// and PLIC flux of the donor.
+template <typename T>
+__global__ void __launch_bounds__(kFaceTile) k_face_flux(const T* __restrict__ cin, const T* __restrict__ ud,
+                                                         Dims g, int d, T sfac, T band,
+                                                         const unsigned long long* __restrict__ list,
+                                                         long long cap, const int* __restrict__ off, int nseg,
+                                                         const int* __restrict__ tile_seg, T* __restrict__ flux) {
     const int n = off[nseg];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const int sgi = segment_of(off, nseg, e);
-        const unsigned long long key = list[(size_t)sgi * cap + (e - off[sgi])];
-        const int f = (int)(key >> 54);
-        const int k = (int)((key >> 36) & 0x3ffffu);
-        const int j = (int)((key >> 18) & 0x3ffffu);
-        const int i = (int)(key & 0x3ffffu);
-        const int x = cell(i, j, k, g);
-        const size_t t = (size_t)f * g.N + x;
-        const T uv = ud[x];
+    for (int base = blockIdx.x * kFaceTile; base < n; base += gridDim.x * kFaceTile) {
+        const int e = base + threadIdx.x;
+        if (e >= n) continue;
+        const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
+        T uv;
+        const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
         const T s = uv * sfac;
-        const int donor = vsign(uv) > 0 ? step_cell(x, i, j, k, d, -1, g) : x;
         T st[27];
-        gather_stencil(cin + (size_t)f * g.N, donor, g, st);
+        gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
         T m[3];
         myc_normal(st, m);
         const T alpha = plic_alpha_banded(m[0], m[1], m[2], st[13], band);
-        flux[t] = face_flux(m, alpha, d, s);
+        flux[fc.t] = face_flux(m, alpha, d, s);
     }
 }
 
@@ -363,18 +395,24 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
             const T* udn = u + (size_t)dn * g.N;
             const int cur = a.list_cur, nxt = 1 - a.list_cur;
             if (a.prof) a.prof->begin(P_FACE_FLUX);
-            scan_counts(counts[cur], a.offsets, gb, a.stream);
+            scan_face_counts(counts[cur], a.offsets, gb, a.tile_seg, a.tile_cap, a.stream);
             bool learned = false;
             if constexpr (std::is_same<T, float>::value) {
                 if (a.mlp) {
+                    // network normals of the listed faces (tensor cores), then the judged fluxes
                     learned = true;
-                    face_flux_learned(ins[sw], ud, g, d, sfac, band, lists[cur], cap, a.offsets, gb, fl, a.mlp,
-                                      a.mlp_tol, a.mlp_status, a.mlp_counters, a.stream);
+                    if (a.prof) { a.prof->end(); a.prof->begin(P_NET_NORMALS); }
+                    face_normals_net(ins[sw], ud, g, d, lists[cur], cap, a.offsets, gb, a.tile_seg, a.net,
+                                     a.mlp, a.mlp_status, a.stream);
+                    if (a.prof) { a.prof->end(); a.prof->begin(P_FACE_FLUX); }
+                    face_flux_judged(ins[sw], ud, g, d, sfac, band, lists[cur], cap, a.offsets, gb, a.tile_seg,
+                                     fl, a.net, a.mlp_tol, a.mlp_counters, a.stream);
+                    if (a.launches) *a.launches += 1;
                 }
             }
             if (!learned)
-                k_face_flux<T><<<152 * 16, 128, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur], cap,
-                                                                a.offsets, gb, fl);
+                k_face_flux<T><<<152 * 16, kFaceTile, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur],
+                                                                      cap, a.offsets, gb, a.tile_seg, fl);
             if (a.prof) { a.prof->end(); a.prof->begin(P_UPDATE); }
             k_update<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac, tau, fl,
                                                              a.ccbits, a.occbits, lists[nxt], cap, counts[nxt],

@@ -42,6 +42,8 @@ enum Slot {
     S_HIST_R,
     S_HIST_RT,
     S_MOM,
+    S_NET,
+    S_TILESEG,
     S_COUNT
 };
 
@@ -88,6 +90,11 @@ bool config_valid(const vof_config* c) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Tiles of a face list at its largest (the list's reserved span).
+size_t tile_cap_for(size_t K, size_t words) {
+    return (2 * 32 * K * (words + (size_t)kSweepBlocks) + kFaceTile - 1) / kFaceTile;
+}
+
 Layout layout_for(const vof_config* c) {
     Layout L;
     Dims g = make_dims(c->nx, c->ny, c->nz);
@@ -126,6 +133,10 @@ Layout layout_for(const vof_config* c) {
     L.size[S_HIST_R] = (size_t)(c->stats_rbins + 1) * 8;
     L.size[S_HIST_RT] = (size_t)(c->stats_rbins + 1) * c->stats_tbins * 8;
     L.size[S_MOM] = 16 * 8;
+    // network normal at the cell of every listed face (learned normal only)
+    L.size[S_NET] = c->precision == VOF_MIXED_LEARNED ? K * N * 16 : 0;
+    // first segment of each tile of kFaceTile entries of a face list
+    L.size[S_TILESEG] = (tile_cap_for(K, words) + 1) * 4;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
         L.off[s] = o;
@@ -510,6 +521,10 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     a.launches = &ctx->launches;
     a.prof = &ctx->prof;
     a.mlp = (const MlpBlob*)ctx->mlp;
+    a.net = ctx->slot<float4>(S_NET);
+    a.tile_seg = ctx->slot<int>(S_TILESEG);
+    a.tile_cap = (int)std::min<size_t>(tile_cap_for(ctx->cfg.k_capacity, (size_t)ctx->g.rows * ctx->g.W),
+                                       (size_t)INT32_MAX);
     a.mlp_tol = (float)ctx->mlp_tol;
     a.mlp_status = (int*)(ctx->misc() + kMiscMlpStatus);
     a.mlp_counters = mlp_counters;
@@ -887,7 +902,7 @@ vof_status vof_profile_read(vof_ctx* ctx, int64_t* launches, double* ms, int32_t
 const char* vof_profile_class_name(int32_t cls) {
     static const char* names[P_COUNT] = {"list_faces", "face_flux", "update", "pack_bits", "near_contact",
                                          "label",      "pairs",     "touch",  "move",      "stats",
-                                         "misc"};
+                                         "misc",       "net_normals"};
     if (cls < 0 || cls >= P_COUNT) return nullptr;
     return names[cls];
 }

@@ -1,30 +1,33 @@
-// Face fluxes of one split sweep with the learned normal (FP32 path; the
-// normal estimator itself has no counterpart in the paper, the fluxes are
-// those of Section 2.2).
+// Fluxes of one split sweep with the learned normal (FP32 path; the
+// estimator has no counterpart in the paper, the fluxes are Section 2.2's).
 //
-// A CTA of 128 threads takes 128 listed faces at a time.  Each thread
-// gathers the 3x3x3 stencil of its face's upwind donor and writes the
-// canonical input row; the CTA runs the network on the tensor cores; each
-// thread maps its output back and judges it: the network's normal is kept
-// when its plane explains the stencil with a mean residual of at most `tol`,
-// or no worse than MYC's plane does, otherwise MYC's normal is used.  Then
-// the plane constant (FP64 refinement near c = 0 or 1) and the PLIC volume
-// of the swept sub-cell, as in the MYC path.
+// k_face_normals_net: a CTA of 128 threads takes 128 consecutive listed
+// faces at a time: each thread gathers the 3x3x3 stencil of its face's
+// upwind donor and writes the canonical input row, the CTA runs the network
+// on the tensor cores, and each thread maps its output back to the grid
+// frame and stores it at the face's cell.
+//
+// k_face_flux_judged: the same tiles at full occupancy.  Every thread judges
+// its network normal (27-cell residual against the tolerance); the faces
+// that need MYC's normal and its residual are compacted to the first
+// threads of the CTA so that the fallback runs on full warps; then every
+// thread takes its plane constant and flux.
 #include "advect_impl.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"
 
 namespace vof {
 
-__global__ void __launch_bounds__(128, 3) k_face_flux_learned(const float* __restrict__ cin,
-                                                              const float* __restrict__ ud, Dims g, int d,
-                                                              float sfac, float band,
-                                                              const unsigned long long* __restrict__ list,
-                                                              long long cap, const int* __restrict__ off, int nseg,
-                                                              float* __restrict__ flux,
-                                                              const MlpBlob* __restrict__ w, float tol,
-                                                              int* __restrict__ status,
-                                                              unsigned long long* __restrict__ counters) {
+static_assert(kFaceTile == 128, "one face per thread of a 128-thread CTA");
+
+__global__ void __launch_bounds__(128, 3) k_face_normals_net(const float* __restrict__ cin,
+                                                             const float* __restrict__ ud, Dims g, int d,
+                                                             const unsigned long long* __restrict__ list,
+                                                             long long cap, const int* __restrict__ off,
+                                                             int nseg, const int* __restrict__ tile_seg,
+                                                             float4* __restrict__ net,
+                                                             const MlpBlob* __restrict__ w,
+                                                             int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
     mlp_cta_begin(s, w);
@@ -32,27 +35,18 @@ __global__ void __launch_bounds__(128, 3) k_face_flux_learned(const float* __res
     uint32_t phase = 0;
     const int t = threadIdx.x;
     const int n = off[nseg];
-    unsigned n_net = 0, n_myc = 0;
     // the loop bound is the same for every thread of the CTA
     for (int base = blockIdx.x * 128; base < n; base += gridDim.x * 128) {
         const int e = base + t;
         const bool valid = e < n;
         float st[27];
-        float sv = 0.f;
         size_t fi = 0;
         if (valid) {
-            const int sgi = segment_of(off, nseg, e);
-            const unsigned long long key = list[(size_t)sgi * cap + (e - off[sgi])];
-            const int f = (int)(key >> 54);
-            const int k = (int)((key >> 36) & 0x3ffffu);
-            const int j = (int)((key >> 18) & 0x3ffffu);
-            const int i = (int)(key & 0x3ffffu);
-            const int x = cell(i, j, k, g);
-            fi = (size_t)f * g.N + x;
-            const float uv = ud[x];
-            sv = uv * sfac;
-            const int donor = vsign(uv) > 0 ? step_cell(x, i, j, k, d, -1, g) : x;
-            gather_stencil(cin + (size_t)f * g.N, donor, g, st);
+            const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
+            float uv;
+            const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
+            fi = fc.t;
+            gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
         } else {
 #pragma unroll
             for (int q = 0; q < 27; ++q) st[q] = 0.5f;
@@ -67,14 +61,96 @@ __global__ void __launch_bounds__(128, 3) k_face_flux_learned(const float* __res
         if (valid) {
             float nn[3];
             canon_output(oc, fr, nn);
+            net[fi] = make_float4(nn[0], nn[1], nn[2], 0.f);
+        }
+    }
+    mlp_cta_end(s, status);
+}
+
+__global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restrict__ cin,
+                                                          const float* __restrict__ ud, Dims g, int d, float sfac,
+                                                          float band, const unsigned long long* __restrict__ list,
+                                                          long long cap, const int* __restrict__ off, int nseg,
+                                                          const int* __restrict__ tile_seg,
+                                                          float* __restrict__ flux,
+                                                          const float4* __restrict__ net, float tol,
+                                                          unsigned long long* __restrict__ counters) {
+    __shared__ float s_st[27][128];  // stencil of thread t's donor in column t
+    __shared__ float s_m[3][128];    // MYC's normal where it replaces the network's
+    __shared__ float s_enet[128];
+    __shared__ int s_list[128];
+    __shared__ unsigned char s_myc[128];
+    __shared__ int s_nf;
+    const int t = threadIdx.x;
+    const int n = off[nseg];
+    unsigned n_net = 0, n_myc = 0;
+    for (int base = blockIdx.x * 128; base < n; base += gridDim.x * 128) {
+        const int e = base + t;
+        const bool valid = e < n;
+        if (t == 0) s_nf = 0;
+        float sv = 0.f, nn[3] = {0.f, 0.f, 0.f};
+        size_t fi = 0;
+        if (valid) {
+            const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
+            float uv;
+            const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
+            sv = uv * sfac;
+            fi = fc.t;
+            float st[27];
+            gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) s_st[q][t] = st[q];
+            const float4 nv = net[fi];
+            nn[0] = nv.x;
+            nn[1] = nv.y;
+            nn[2] = nv.z;
+        }
+        s_myc[t] = 0;
+        __syncthreads();
+        // network residual of every face; the ones above the tolerance queue
+        bool keep = true;
+        if (valid) {
+            const float e_net = normal_residual_s<128>(&s_st[0][t], nn);
+            keep = e_net <= tol;
+            if (!keep) {
+                s_enet[t] = e_net;
+                s_list[atomicAdd(&s_nf, 1)] = t;
+            }
+        }
+        __syncthreads();
+        // MYC's normal and residual for the queued faces, on the first threads
+        if (t < s_nf) {
+            const int u = s_list[t];
+            float stl[27], m[3];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) stl[q] = s_st[q][u];
+            myc_normal(stl, m);
+            if (!(s_enet[u] <= normal_residual_s<128>(&s_st[0][u], m))) {
+                s_m[0][u] = m[0];
+                s_m[1][u] = m[1];
+                s_m[2][u] = m[2];
+                s_myc[u] = 1;
+            }
+        }
+        __syncthreads();
+        if (valid) {
             float m[3];
-            if (judged_normal(st, nn, tol, m))
-                ++n_net;
-            else
+            if (s_myc[t]) {
+                m[0] = s_m[0][t];
+                m[1] = s_m[1][t];
+                m[2] = s_m[2][t];
                 ++n_myc;
-            const float alpha = plic_alpha_banded(m[0], m[1], m[2], st[13], band);
+            } else {
+                const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
+                m[0] = nn[0] * inv;
+                m[1] = nn[1] * inv;
+                m[2] = nn[2] * inv;
+                ++n_net;
+            }
+            const float alpha = plic_alpha_banded(m[0], m[1], m[2], s_st[13][t], band);
             flux[fi] = face_flux(m, alpha, d, sv);
         }
+        __syncthreads();  // the tile's shared arrays are reused by the next tile
     }
     n_net = __reduce_add_sync(0xffffffffu, n_net);
     n_myc = __reduce_add_sync(0xffffffffu, n_myc);
@@ -82,19 +158,26 @@ __global__ void __launch_bounds__(128, 3) k_face_flux_learned(const float* __res
         if (n_net) atomicAdd(&counters[0], (unsigned long long)n_net);
         if (n_myc) atomicAdd(&counters[1], (unsigned long long)n_myc);
     }
-    mlp_cta_end(s, status);
 }
 
-void face_flux_learned(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
-                       const unsigned long long* list, long long cap, const int* off, int nseg, float* flux,
-                       const MlpBlob* w, float tol, int* status, unsigned long long* counters, cudaStream_t st) {
+void face_flux_judged(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
+                      const unsigned long long* list, long long cap, const int* off, int nseg, const int* tile_seg,
+                      float* flux, const float4* net, float tol, unsigned long long* counters, cudaStream_t st) {
+    k_face_flux_judged<<<152 * 16, 128, 0, st>>>(cin, ud, g, d, sfac, band, list, cap, off, nseg, tile_seg, flux,
+                                                 net, tol, counters);
+}
+
+void face_normals_net(const float* cin, const float* ud, const Dims& g, int d, const unsigned long long* list,
+                      long long cap, const int* off, int nseg, const int* tile_seg, float4* net, const MlpBlob* w,
+                      int* status, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_face_flux_learned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+        cudaFuncSetAttribute(k_face_normals_net, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(MlpSmem));
         attr = true;
     }
-    k_face_flux_learned<<<152 * 3, 128, sizeof(MlpSmem), st>>>(cin, ud, g, d, sfac, band, list, cap, off, nseg, flux,
-                                                                w, tol, status, counters);
+    k_face_normals_net<<<152 * 3, 128, sizeof(MlpSmem), st>>>(cin, ud, g, d, list, cap, off, nseg, tile_seg, net, w,
+                                                              status);
 }
 
 }  // namespace vof

@@ -23,6 +23,7 @@ enum ProfClass {
     P_MOVE,
     P_STATS,
     P_MISC,
+    P_NET_NORMALS,
     P_COUNT
 };
 
@@ -56,15 +57,26 @@ constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a s
 
 struct AdvectArgs;
 struct MlpBlob;
-// Learned-normal face fluxes of the listed faces of one sweep (FP32 path).
-void face_flux_learned(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
-                       const unsigned long long* list, long long cap, const int* off, int nseg, float* flux,
-                       const MlpBlob* w, float tol, int* status, unsigned long long* counters, cudaStream_t st);
+// Network normal of the donor of every listed face of one sweep (FP32
+// path): net[f * N + x] for the face at cell x of field f.
+void face_normals_net(const float* cin, const float* ud, const Dims& g, int d, const unsigned long long* list,
+                      long long cap, const int* off, int nseg, const int* tile_seg, float4* net, const MlpBlob* w,
+                      int* status, cudaStream_t st);
+// Fluxes of the listed faces with the judged learned normal (network normal
+// net[f * N + x] against MYC's), counters[0/1] += faces on network / MYC.
+void face_flux_judged(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
+                      const unsigned long long* list, long long cap, const int* off, int nseg, const int* tile_seg,
+                      float* flux, const float4* net, float tol, unsigned long long* counters, cudaStream_t st);
 cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps);
 cudaError_t advect_steps_fp32(AdvectArgs& a, int nsteps);
 
 // Exclusive scan of n ints (one block); off[n] = total.
 cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st);
+// Face lists: consumers take tiles of kFaceTile consecutive entries.
+constexpr int kFaceTile = 128;
+// Exclusive scan of the segment lengths of a face list, plus tile_seg[t] =
+// the segment holding entry t * kFaceTile (t < tile_cap).
+cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, int tile_cap, cudaStream_t st);
 cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
                       cudaStream_t st);
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,

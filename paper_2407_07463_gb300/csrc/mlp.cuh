@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "mlp_judge.cuh"
 #include "plic.cuh"
 #include "tc.cuh"
 
@@ -94,25 +95,6 @@ __device__ __forceinline__ void load_weight_pair(unsigned char* tile, const __nv
         *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(o, i, 2 * cols)) = w[idx];
         *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(o, cols + i, 2 * cols)) = w[idx];
     }
-}
-
-// Residual of a normal n on a stencil (judge of the learned normal): the
-// plane of normal n holding the centre cell's volume fraction, extended over
-// the 3x3x3 block; the mean over the 27 cells of |predicted - actual|
-// fraction.  +inf for a zero or non-finite n.
-__device__ __forceinline__ float normal_residual(const float st[27], const float n[3]) {
-    const float l1 = fabsf(n[0]) + fabsf(n[1]) + fabsf(n[2]);
-    if (!(l1 > 0.f) || !isfinite(l1)) return INFINITY;
-    const float m0 = n[0] / l1, m1 = n[1] / l1, m2 = n[2] / l1;
-    const float al = plic_alpha<float>(m0, m1, m2, st[13]);
-    float e = 0.f;
-#pragma unroll 1
-    for (int q = 0; q < 27; ++q) {
-        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float v = plic_volume<float>(m0, m1, m2, al - (m0 * i + m1 * j + m2 * k));
-        e += fabsf(v - st[q]);
-    }
-    return e * (1.f / 27.f);
 }
 
 }  // namespace vof

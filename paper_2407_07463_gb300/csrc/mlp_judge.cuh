@@ -1,0 +1,64 @@
+// Judge of the learned normal (internal; the estimator has no counterpart
+// in the paper): the residual of a normal on its 3x3x3 stencil and the
+// choice between the network's normal and MYC's.
+#pragma once
+
+#include <math.h>
+
+#include "plic.cuh"
+
+namespace vof {
+
+// Residual of a normal n on a stencil: the plane of normal n holding the
+// centre cell's volume fraction, extended over the 3x3x3 block; the mean
+// over the 27 cells of |predicted - actual| fraction.  +inf for a zero or
+// non-finite n.  The reflection and ordering of the normal are done once
+// per stencil and every cell takes the branch-free volume (vol_fast), so
+// all lanes of a warp run the same instructions.  The value of cell q is
+// st[q * STRIDE] (STRIDE > 1: a column of a shared-memory tile).
+template <int STRIDE>
+static __device__ __noinline__ float normal_residual_s(const float* st, const float n[3]) {
+    const float l1 = fabsf(n[0]) + fabsf(n[1]) + fabsf(n[2]);
+    if (!(l1 > 0.f) || !isfinite(l1)) return INFINITY;
+    const float m0 = n[0] / l1, m1 = n[1] / l1, m2 = n[2] / l1;
+    const float al = plic_alpha<float>(m0, m1, m2, st[13 * STRIDE]);
+    // x_i -> 1 - x_i for a negative component moves the constant by |m_i|
+    const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
+    float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
+    sort3(a, b, c);
+    const float S = a + b + c;
+    float e = 0.f;
+#pragma unroll 3
+    for (int q = 0; q < 27; ++q) {
+        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
+        const float v = vol_fast(a, b, c, S, al + off - (m0 * i + m1 * j + m2 * k));
+        e += fabsf(v - st[q * STRIDE]);
+    }
+    return e * (1.f / 27.f);
+}
+
+__device__ __forceinline__ float normal_residual(const float st[27], const float n[3]) {
+    return normal_residual_s<1>(st, n);
+}
+
+// The learned normal as the step uses it: the network's normal nn (original
+// frame) is kept when the residual of its plane is at most tol, or no larger
+// than that of MYC's normal; otherwise MYC's.  m gets the L1-normalised
+// choice; returns true when the network's was kept.
+__device__ __forceinline__ bool judged_normal(const float st[27], const float nn[3], float tol, float m[3]) {
+    const float e_net = normal_residual(st, nn);
+    bool keep = e_net <= tol;
+    if (!keep) {
+        myc_normal(st, m);
+        keep = e_net <= normal_residual(st, m);
+    }
+    if (keep) {
+        const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
+        m[0] = nn[0] * inv;
+        m[1] = nn[1] * inv;
+        m[2] = nn[2] * inv;
+    }
+    return keep;
+}
+
+}  // namespace vof

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "mlp.cuh"
+#include "mlp_judge.cuh"
 #include "plic.cuh"
 #include "tc.cuh"
 
@@ -141,26 +142,6 @@ __device__ __forceinline__ void mlp_cta_end(MlpSmem& s, int* status) {
     tc::fence_after_sync();
     if (threadIdx.x < 32) tc::tmem_dealloc(s.tbase, kTmemCols);
     if (threadIdx.x == 0 && s.timeout && status) atomicExch(status, 1);
-}
-
-// The learned normal as the step uses it: the network's normal nn (original
-// frame) is kept when the mean residual of its plane over the stencil is at
-// most tol, or no larger than that of MYC's normal; otherwise MYC's.  m gets
-// the L1-normalised choice; returns true when the network's was kept.
-__device__ __forceinline__ bool judged_normal(const float st[27], const float nn[3], float tol, float m[3]) {
-    const float e_net = normal_residual(st, nn);
-    bool keep = e_net <= tol;
-    if (!keep) {
-        myc_normal(st, m);
-        keep = e_net <= normal_residual(st, m);
-    }
-    if (keep) {
-        const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
-        m[0] = nn[0] * inv;
-        m[1] = nn[1] * inv;
-        m[2] = nn[2] * inv;
-    }
-    return keep;
 }
 
 }  // namespace vof

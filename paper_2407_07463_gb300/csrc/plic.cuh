@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 namespace vof {
 
 template <typename T>
@@ -76,7 +78,7 @@ __device__ __forceinline__ T area2_d(T a, T b, T beta) {
 // pieces as they are in floating point (their sum, not a, is the divisor):
 // alpha - a rounds, and dividing by a would leave an error of ulp(alpha)/a.
 template <typename T>
-__device__ T vol_sorted(T a, T b, T c, T alpha) {
+__device__ __noinline__ T vol_sorted(T a, T b, T c, T alpha) {
     T lo = alpha - a, hi = alpha;
     if (a <= PlicConst<T>::tiny || !(hi > lo)) return area2(b, c, alpha);
     T acc = T(0), wsum = T(0);
@@ -127,15 +129,50 @@ __device__ __forceinline__ void sort3(T& a, T& b, T& c) {
     if (a > b) { t = a; a = b; b = t; }
 }
 
+// Branch-free FP32 volume for sorted 0 <= a <= b <= c (c > 0), S = a+b+c,
+// any alpha.  The inclusion-exclusion closed form
+//   V = sum over the 8 vertex sums s of (-1)^|s| (alpha - s)_+^3 / (6abc)
+// is rewritten as nested divided differences of P(x) = x_+^3,
+//   V = [H(alpha) - H(alpha - c)] / (6c),  H(x) = [D(x) - D(x - b)] / b,
+//   D(x) = [P(x) - P(x - a)] / a,
+// each taken in the form that has no cancellation: D(x) = 3x^2 - 3xa + a^2
+// when x >= a (else x^3 / a, or 0), H(x) = 3(2x - b - a) when x - b >= a
+// (else the plain difference, whose terms are then O(b^2)), and the
+// derivatives of D in the limit b -> 0.  With V(alpha) = 1 - V(S - alpha)
+// for alpha > S/2 the result is within a few ulp of the exact volume for
+// every normal, including a = 0 and a = b = 0 (no division by a small
+// product, unlike the closed form itself).
+__device__ __forceinline__ float vdd1(float x, float a) {
+    const float p = 3.f * x * x - 3.f * x * a + a * a;
+    const float q = x > 0.f ? x * x * x / a : 0.f;
+    return x >= a ? p : q;
+}
+__device__ __forceinline__ float vdd1_d(float x, float a) {
+    return x >= a ? 6.f * x - 3.f * a : (x > 0.f ? 3.f * x * x / a : 0.f);
+}
+__device__ __forceinline__ float vdd2(float x, float a, float b) {
+    const float lin = 3.f * (2.f * x - b - a);
+    const float dir = (vdd1(x, a) - vdd1(x - b, a)) / b;
+    return b <= 1e-30f ? vdd1_d(x, a) : (x - b >= a ? lin : dir);
+}
+__device__ __forceinline__ float vol_fast(float a, float b, float c, float S, float alpha) {
+    const bool flip = 2.f * alpha > S;
+    const float x = flip ? S - alpha : alpha;
+    const float v = (vdd2(x, a, b) - vdd2(x - c, a, b)) / (6.f * c);
+    const float r = flip ? 1.f - v : v;
+    return alpha <= 0.f ? 0.f : (alpha >= S ? 1.f : r);
+}
+
 // Volume of {x in [0,1]^3 : m.x < alpha}.
 template <typename T>
-__device__ T plic_volume(T m0, T m1, T m2, T alpha) {
+__device__ __noinline__ T plic_volume(T m0, T m1, T m2, T alpha) {
     if (m0 < T(0)) { alpha -= m0; m0 = -m0; }
     if (m1 < T(0)) { alpha -= m1; m1 = -m1; }
     if (m2 < T(0)) { alpha -= m2; m2 = -m2; }
     sort3(m0, m1, m2);
     T S = m0 + m1 + m2;
     if (S <= T(0)) return alpha > T(0) ? T(1) : T(0);
+    if constexpr (std::is_same<T, float>::value) return vol_fast(m0, m1, m2, S, alpha);
     if (alpha <= T(0)) return T(0);
     if (alpha >= S) return T(1);
     if (T(2) * alpha > S) return T(1) - vol_sorted(m0, m1, m2, S - alpha);
@@ -146,7 +183,7 @@ __device__ T plic_volume(T m0, T m1, T m2, T alpha) {
 // *region (if not null) receives the piece the root lies in: 0 for the 2D
 // cases (a = 0), 1..4 the cubic regions, 5 the prism region.
 template <typename T>
-__device__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr) {
+__device__ __noinline__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr) {
     T al;
     int reg;
     if (a <= PlicConst<T>::tiny) {
@@ -243,7 +280,7 @@ __device__ __forceinline__ double alpha_refine_fp64(double a, double b, double c
 
 // Plane constant alpha with plic_volume(m, alpha) = cv.
 template <typename T>
-__device__ T plic_alpha(T m0, T m1, T m2, T cv) {
+__device__ __noinline__ T plic_alpha(T m0, T m1, T m2, T cv) {
     T off = T(0);
     if (m0 < T(0)) { off += m0; m0 = -m0; }
     if (m1 < T(0)) { off += m1; m1 = -m1; }

@@ -334,6 +334,57 @@ cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Exclusive scan of the face-list segment lengths, then the segment holding
+// the first entry of every tile of kFaceTile consecutive entries:
+// tile_seg[t] = s with off[s] <= t * kFaceTile < off[s + 1] (at most
+// tile_cap tiles are recorded).
+__global__ void __launch_bounds__(1024) k_scan_faces(const int* __restrict__ counts, int* __restrict__ off, int n,
+                                                     int* __restrict__ tile_seg, int tile_cap) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? counts[i] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int s0 = wsum[lane];
+            int si = s0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) si += t;
+            }
+            wsum[lane] = si - s0;
+        }
+        __syncthreads();
+        const int excl = carry + wsum[wid] + incl - v;
+        if (i < n) {
+            off[i] = excl;
+            // tiles whose first entry lies in this segment
+            const int t0 = (excl + kFaceTile - 1) / kFaceTile;
+            const int t1 = min((excl + v + kFaceTile - 1) / kFaceTile, tile_cap);
+            for (int t = t0; t < t1; ++t) tile_seg[t] = i;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, int tile_cap, cudaStream_t st) {
+    k_scan_faces<<<1, 1024, 0, st>>>(counts, off, n, tile_seg, tile_cap);
+    return cudaGetLastError();
+}
+
 // Labels of one row segment per warp: 0 for empty cells, 1 + rank of the
 // root for occupied ones.
 __global__ void k_ccl_relabel(const uint32_t* __restrict__ bits_f, const int* __restrict__ parent,
