@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "plic.cuh"
+#include "update_vec.cuh"
 
 namespace vof {
 
@@ -112,12 +113,6 @@ struct WordWalk {
     }
 };
 
-// Face-list entry: the face is the low face (along the sweep) of cell
-// (i, j, k) of field f, packed so that decoding needs no division.
-__device__ __forceinline__ unsigned long long face_key(int f, int i, int j, int k) {
-    return ((unsigned long long)f << 54) | ((unsigned long long)k << 36) | ((unsigned long long)j << 18) |
-           (unsigned long long)i;
-}
 
 // Warp-aggregated append to a block's shared counter; every lane calls it.
 __device__ __forceinline__ int block_append(bool flag, int* s_count) {
@@ -369,9 +364,18 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
     // persistent-size grid: as many (32 x K)-thread blocks as fit on the
     // SMs at 64 registers per thread, each walking a long range of words
     const int per_sm = std::max(1, std::min(32, 32 / a.K));
-    const int gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
-    // list segment per block: at most 2 faces per cell and field
-    const long long cap = 2LL * 32 * a.K * ((words + gb - 1) / gb);  // words per block = ceil(words / gb)
+    // rows of whole 32-cell words take the vectorised update (16-byte lanes)
+    const bool vec = g.nx % 32 == 0;
+    int gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
+    if (vec) gb = std::min(gb, 2048);
+    // list segment per block: at most 2 faces per cell and field of the
+    // block's cells (words per block = ceil(words / gb); chunks of 32 * VW
+    // cells for the vectorised pass); gb * cap stays within the reserved span
+    long long cap = 2LL * 32 * a.K * ((words + gb - 1) / gb);
+    if (vec) {
+        const long long CH = 32LL * VecOf<T>::W, nch = ((long long)g.N + CH - 1) / CH;
+        cap = std::max(cap, 2LL * a.K * CH * ((nch + gb - 1) / gb));
+    }
     // second list after the first list's reserved span (see the workspace layout)
     unsigned long long* lists[2] = {a.list, a.list + (size_t)2 * 32 * a.Kcap * ((size_t)words + kSweepBlocks)};
     int* counts[2] = {a.counts, a.counts + kSweepBlocks};
@@ -414,9 +418,14 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
                 k_face_flux<T><<<152 * 16, kFaceTile, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur],
                                                                       cap, a.offsets, gb, a.tile_seg, fl);
             if (a.prof) { a.prof->end(); a.prof->begin(P_UPDATE); }
-            k_update<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac, tau, fl,
-                                                             a.ccbits, a.occbits, lists[nxt], cap, counts[nxt],
-                                                             a.clipped);
+            if (vec)
+                k_update_vec<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac,
+                                                                     tau, fl, a.ccbits, a.occbits, lists[nxt], cap,
+                                                                     counts[nxt], a.clipped);
+            else
+                k_update<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac, tau,
+                                                                 fl, a.ccbits, a.occbits, lists[nxt], cap, counts[nxt],
+                                                                 a.clipped);
             if (a.prof) a.prof->end();
             a.list_cur = nxt;
             if (a.launches) *a.launches += 3;  // scan, flux, update

@@ -43,6 +43,13 @@ __device__ __forceinline__ int cell(int i, int j, int k, const Dims& g) {
     return (k * g.ny + j) * g.nx + i;
 }
 
+// Face-list entry: the face is the low face (along a sweep) of cell
+// (i, j, k) of field f, packed so that decoding needs no division.
+__device__ __forceinline__ unsigned long long face_key(int f, int i, int j, int k) {
+    return ((unsigned long long)f << 54) | ((unsigned long long)k << 36) | ((unsigned long long)j << 18) |
+           (unsigned long long)i;
+}
+
 // Neighbour of x one cell along axis d in direction dir (+1/-1), periodic.
 __device__ __forceinline__ int step_cell(int x, int i, int j, int k, int d, int dir, const Dims& g) {
     if (d == 0) {

@@ -174,6 +174,25 @@ def test_fused_mixed_steps(vof, shape, steps):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape", [(3, 5, 64), (9, 1, 96), (4, 6, 32), (2, 2, 128)])
+def test_vectorised_rows_match_oracle(vof, precision, shape):
+    """Rows of whole 32-cell words take the 16-byte-lane update: a partial
+    last chunk, a single row per plane (the y neighbour is the cell itself),
+    periodic wrap along x inside a warp, every sweep order."""
+    c, u, dt, _ = make_case(shape, 2, 1.5, seed=sum(shape) + precision, cfl=0.3)
+    if precision:
+        c = c.astype(np.float32).astype(np.float64)
+        u = u.astype(np.float32).astype(np.float64)
+    ctx, c_d, _, rep = run_gpu(vof, c, u, dt, 3, precision=precision)
+    want, clipped = O.advect(c, u, dt, 1.0, 3)
+    got = c_d.cpu().numpy().astype(np.float64)
+    assert np.abs(got - want).max() <= (TOL64 if precision == 0 else TOL32)
+    if precision == 0:
+        assert abs(rep["clipped_volume"] - clipped.sum()) <= 1e-12
+    ctx.close()
+
+
 def test_fused_bits_feed_recolour(vof):
     """Step 1 after a fused step uses the occupancy bits the step wrote; the
     recolouring of the GPU's own field must equal the oracle's."""
