@@ -367,7 +367,14 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
     // rows of whole 32-cell words take the vectorised update (16-byte lanes)
     const bool vec = g.nx % 32 == 0;
     int gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
-    if (vec) gb = std::min(gb, 2048);
+    if (vec) {
+        // one resident wave of (32 x K)-thread blocks
+        int resident = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_update_vec<T>, 32 * a.K, 0) != cudaSuccess ||
+            resident < 1)
+            resident = per_sm;
+        gb = std::min(152 * resident, 2048);
+    }
     // list segment per block: at most 2 faces per cell and field of the
     // block's cells (words per block = ceil(words / gb); chunks of 32 * VW
     // cells for the vectorised pass); gb * cap stays within the reserved span

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
                                                           const float4* __restrict__ net, float tol,
                                                           unsigned long long* __restrict__ counters) {
     __shared__ float s_st[27][128];  // stencil of thread t's donor in column t
-    __shared__ float s_m[3][128];    // MYC's normal where it replaces the network's
+    __shared__ float s_m[4][128];    // MYC's normal and plane constant where it replaces the network's
     __shared__ float s_enet[128];
     __shared__ int s_list[128];
     __shared__ unsigned char s_myc[128];
@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
         const int e = base + t;
         const bool valid = e < n;
         if (t == 0) s_nf = 0;
-        float sv = 0.f, nn[3] = {0.f, 0.f, 0.f};
+        float sv = 0.f, mn[3] = {1.f, 0.f, 0.f};
+        bool net_ok = false;
         size_t fi = 0;
         if (valid) {
             const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
@@ -101,18 +102,16 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
 #pragma unroll
             for (int q = 0; q < 27; ++q) s_st[q][t] = st[q];
             const float4 nv = net[fi];
-            nn[0] = nv.x;
-            nn[1] = nv.y;
-            nn[2] = nv.z;
+            const float nn[3] = {nv.x, nv.y, nv.z};
+            net_ok = l1_normalise(nn, mn);
         }
         s_myc[t] = 0;
         __syncthreads();
         // network residual of every face; the ones above the tolerance queue
-        bool keep = true;
+        float al = 0.f;
         if (valid) {
-            const float e_net = normal_residual_s<128>(&s_st[0][t], nn);
-            keep = e_net <= tol;
-            if (!keep) {
+            const float e_net = net_ok ? normal_residual_m<128>(&s_st[0][t], mn, &al) : INFINITY;
+            if (!(e_net <= tol)) {
                 s_enet[t] = e_net;
                 s_list[atomicAdd(&s_nf, 1)] = t;
             }
@@ -121,14 +120,15 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
         // MYC's normal and residual for the queued faces, on the first threads
         if (t < s_nf) {
             const int u = s_list[t];
-            float stl[27], m[3];
+            float stl[27], m[3], am;
 #pragma unroll
             for (int q = 0; q < 27; ++q) stl[q] = s_st[q][u];
             myc_normal(stl, m);
-            if (!(s_enet[u] <= normal_residual_s<128>(&s_st[0][u], m))) {
+            if (!(s_enet[u] <= normal_residual_m<128>(&s_st[0][u], m, &am))) {
                 s_m[0][u] = m[0];
                 s_m[1][u] = m[1];
                 s_m[2][u] = m[2];
+                s_m[3][u] = am;
                 s_myc[u] = 1;
             }
         }
@@ -139,16 +139,18 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
                 m[0] = s_m[0][t];
                 m[1] = s_m[1][t];
                 m[2] = s_m[2][t];
+                al = s_m[3][t];
                 ++n_myc;
             } else {
-                const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
-                m[0] = nn[0] * inv;
-                m[1] = nn[1] * inv;
-                m[2] = nn[2] * inv;
+                m[0] = mn[0];
+                m[1] = mn[1];
+                m[2] = mn[2];
                 ++n_net;
             }
-            const float alpha = plic_alpha_banded(m[0], m[1], m[2], s_st[13][t], band);
-            flux[fi] = face_flux(m, alpha, d, sv);
+            // the residual's FP32 plane constant, refined in FP64 near c = 0 or 1
+            const float cv = s_st[13][t];
+            if (cv < band || cv > 1.f - band) al = plic_alpha_banded(m[0], m[1], m[2], cv, band);
+            flux[fi] = face_flux(m, al, d, sv);
         }
         __syncthreads();  // the tile's shared arrays are reused by the next tile
     }

@@ -9,19 +9,28 @@
 
 namespace vof {
 
-// Residual of a normal n on a stencil: the plane of normal n holding the
-// centre cell's volume fraction, extended over the 3x3x3 block; the mean
-// over the 27 cells of |predicted - actual| fraction.  +inf for a zero or
-// non-finite n.  The reflection and ordering of the normal are done once
-// per stencil and every cell takes the branch-free volume (vol_fast), so
-// all lanes of a warp run the same instructions.  The value of cell q is
-// st[q * STRIDE] (STRIDE > 1: a column of a shared-memory tile).
-template <int STRIDE>
-static __device__ __noinline__ float normal_residual_s(const float* st, const float n[3]) {
+// L1-normalised copy of a normal; false for a zero or non-finite one.
+__device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
     const float l1 = fabsf(n[0]) + fabsf(n[1]) + fabsf(n[2]);
-    if (!(l1 > 0.f) || !isfinite(l1)) return INFINITY;
-    const float m0 = n[0] / l1, m1 = n[1] / l1, m2 = n[2] / l1;
+    if (!(l1 > 0.f) || !isfinite(l1)) return false;
+    m[0] = n[0] / l1;
+    m[1] = n[1] / l1;
+    m[2] = n[2] / l1;
+    return true;
+}
+
+// Residual of an L1-normalised normal m on a stencil: the plane of normal m
+// holding the centre cell's volume fraction, extended over the 3x3x3 block;
+// the mean over the 27 cells of |predicted - actual| fraction.  *alpha gets
+// that plane's constant (FP32).  The reflection and ordering of the normal
+// are done once per stencil and every cell takes the branch-free volume
+// (vol_fast), so all lanes of a warp run the same instructions.  The value
+// of cell q is st[q * STRIDE] (STRIDE > 1: a column of a shared-memory tile).
+template <int STRIDE>
+static __device__ __noinline__ float normal_residual_m(const float* st, const float m[3], float* alpha) {
+    const float m0 = m[0], m1 = m[1], m2 = m[2];
     const float al = plic_alpha<float>(m0, m1, m2, st[13 * STRIDE]);
+    *alpha = al;
     // x_i -> 1 - x_i for a negative component moves the constant by |m_i|
     const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
@@ -37,26 +46,29 @@ static __device__ __noinline__ float normal_residual_s(const float* st, const fl
     return e * (1.f / 27.f);
 }
 
+// Residual of any normal n (+inf for a zero or non-finite one).
 __device__ __forceinline__ float normal_residual(const float st[27], const float n[3]) {
-    return normal_residual_s<1>(st, n);
+    float m[3], al;
+    if (!l1_normalise(n, m)) return INFINITY;
+    return normal_residual_m<1>(st, m, &al);
 }
 
 // The learned normal as the step uses it: the network's normal nn (original
-// frame) is kept when the residual of its plane is at most tol, or no larger
-// than that of MYC's normal; otherwise MYC's.  m gets the L1-normalised
-// choice; returns true when the network's was kept.
+// frame, L1-normalised by division) is kept when the residual of its plane
+// is at most tol, or no larger than that of MYC's normal; otherwise MYC's.
+// m gets the choice; returns true when the network's was kept.
 __device__ __forceinline__ bool judged_normal(const float st[27], const float nn[3], float tol, float m[3]) {
-    const float e_net = normal_residual(st, nn);
+    float mn[3], al;
+    const float e_net = l1_normalise(nn, mn) ? normal_residual_m<1>(st, mn, &al) : INFINITY;
     bool keep = e_net <= tol;
     if (!keep) {
         myc_normal(st, m);
-        keep = e_net <= normal_residual(st, m);
+        keep = e_net <= normal_residual_m<1>(st, m, &al);
     }
     if (keep) {
-        const float inv = 1.f / (fabsf(nn[0]) + fabsf(nn[1]) + fabsf(nn[2]));
-        m[0] = nn[0] * inv;
-        m[1] = nn[1] * inv;
-        m[2] = nn[2] * inv;
+        m[0] = mn[0];
+        m[1] = mn[1];
+        m[2] = mn[2];
     }
     return keep;
 }

@@ -103,9 +103,10 @@ __global__ void __launch_bounds__(512, 2)
     const int plane = g.nx * g.ny;
     double removed = 0.0;
     const int nchunks = (g.N + CH - 1) / CH;
-    const int per = (nchunks + gridDim.x - 1) / gridDim.x;
-    const int cbeg = blockIdx.x * per, cend = min(cbeg + per, nchunks);
-    for (int chk = cbeg; chk < cend; ++chk) {
+    // grid-stride over the chunks: at any time the blocks work on one band
+    // of consecutive chunks, so the neighbouring rows and planes a chunk
+    // reads were read from DRAM by the band just before (L2 reuse)
+    for (int chk = blockIdx.x; chk < nchunks; chk += gridDim.x) {
         const int xv = chk * CH + lane * VW;
         const bool valid = xv < g.N;
         // lanes past the end of the grid work on cell 0 (every index stays in
