@@ -23,8 +23,9 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 // holding the centre cell's volume fraction, extended over the 3x3x3 block;
 // the mean over the 27 cells of |predicted - actual| fraction.  *alpha gets
 // that plane's constant (FP32).  The reflection and ordering of the normal
-// are done once per stencil and every cell takes the branch-free volume
-// (vol_fast), so all lanes of a warp run the same instructions.  The value
+// are done once per stencil (with the reciprocals the volume needs) and
+// every cell takes the branch-free volume (vol_fast_r), so all lanes of a
+// warp run the same instructions.  The value
 // of cell q is st[q * STRIDE] (STRIDE > 1: a column of a shared-memory tile).
 template <int STRIDE>
 static __device__ __noinline__ float normal_residual_m(const float* st, const float m[3], float* alpha) {
@@ -35,12 +36,12 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
     const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
     sort3(a, b, c);
-    const float S = a + b + c;
+    const VolRecip r = vol_recip(a, b, c);
     float e = 0.f;
 #pragma unroll 3
     for (int q = 0; q < 27; ++q) {
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float v = vol_fast(a, b, c, S, al + off - (m0 * i + m1 * j + m2 * k));
+        const float v = vol_fast_r(r, al + off - (m0 * i + m1 * j + m2 * k));
         e += fabsf(v - st[q * STRIDE]);
     }
     return e * (1.f / 27.f);

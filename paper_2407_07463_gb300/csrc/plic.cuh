@@ -163,6 +163,44 @@ __device__ __forceinline__ float vol_fast(float a, float b, float c, float S, fl
     return alpha <= 0.f ? 0.f : (alpha >= S ? 1.f : r);
 }
 
+// The same with the reciprocals of one normal taken once (many plane
+// constants per normal): ia = 1/a, ib = 1/b, i6c = 1/(6c); a product
+// replaces each division (results within a few ulp of vol_fast's).
+struct VolRecip {
+    float a, b, c, S, ia, ib, i6c;
+    bool b0;  // b <= 1e-30: the b -> 0 limit
+};
+__device__ __forceinline__ VolRecip vol_recip(float a, float b, float c) {
+    VolRecip r;
+    r.a = a;
+    r.b = b;
+    r.c = c;
+    r.S = a + b + c;
+    r.ia = 1.f / a;
+    r.ib = 1.f / b;
+    r.i6c = 1.f / (6.f * c);
+    r.b0 = b <= 1e-30f;
+    return r;
+}
+__device__ __forceinline__ float vdd1r(float x, float a, float ia) {
+    const float p = 3.f * x * x - 3.f * x * a + a * a;
+    const float q = x > 0.f ? x * x * x * ia : 0.f;
+    return x >= a ? p : q;
+}
+__device__ __forceinline__ float vdd2r(float x, const VolRecip& r) {
+    const float lin = 3.f * (2.f * x - r.b - r.a);
+    const float dir = (vdd1r(x, r.a, r.ia) - vdd1r(x - r.b, r.a, r.ia)) * r.ib;
+    const float der = x >= r.a ? 6.f * x - 3.f * r.a : (x > 0.f ? 3.f * x * x * r.ia : 0.f);
+    return r.b0 ? der : (x - r.b >= r.a ? lin : dir);
+}
+__device__ __forceinline__ float vol_fast_r(const VolRecip& r, float alpha) {
+    const bool flip = 2.f * alpha > r.S;
+    const float x = flip ? r.S - alpha : alpha;
+    const float v = (vdd2r(x, r) - vdd2r(x - r.c, r)) * r.i6c;
+    const float res = flip ? 1.f - v : v;
+    return alpha <= 0.f ? 0.f : (alpha >= r.S ? 1.f : res);
+}
+
 // Volume of {x in [0,1]^3 : m.x < alpha}.
 template <typename T>
 __device__ __noinline__ T plic_volume(T m0, T m1, T m2, T alpha) {
