@@ -4,5 +4,8 @@
 #include "advect_impl.cuh"
 
 namespace vof {
-cudaError_t advect_steps_fp32(AdvectArgs& a, int nsteps) { return advect_steps_t<float>(a, nsteps); }
+cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps) { return advect_set(S, a, nsteps); }
+cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps) {
+    return advect_set(S, a, nsteps);
+}
 }  // namespace vof

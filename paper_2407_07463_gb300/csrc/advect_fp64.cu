@@ -4,5 +4,8 @@
 #include "advect_impl.cuh"
 
 namespace vof {
-cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps) { return advect_steps_t<double>(a, nsteps); }
+cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps) { return advect_set(S, a, nsteps); }
+cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps) {
+    return advect_set(S, a, nsteps);
+}
 }  // namespace vof

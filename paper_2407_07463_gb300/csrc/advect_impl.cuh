@@ -26,60 +26,39 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "boxes.cuh"
+#include "faces.cuh"
 #include "plic.cuh"
 #include "update_vec.cuh"
 
 namespace vof {
 
-struct AdvectArgs {
-    Dims g;
-    int K;                       // fields advected (the active ones)
-    int Kcap;                    // fields stored (sizes the face lists)
-    void* c;                     // [K][N] state, updated in place
-    const void* u;               // [3][N]
-    void* buf1;                  // [K][N] scratch
-    void* buf2;                  // [K][N] scratch
-    void* flux;                  // [K][N] scratch (listed faces only)
-    unsigned long long* list;    // [2][K*N] face lists (current, next), segmented by block
+// Buffers and settings shared by the boxes of one advance (internal).
+struct SweepArgs {
+    unsigned long long* list;    // two face lists of list_entries entries each, segmented by block
+    long long list_entries;      // reserved entries per list
     int* counts;                 // [2][kSweepBlocks] segment lengths
     int* offsets;                // [kSweepBlocks + 1] scan of the current counts
-    uint32_t* ccbits;            // [K][rows][W] c > 1/2 at the step start
-    uint32_t* occbits;           // [K][rows][W] occupancy after the step
-    double* clipped;             // [K] accumulated clip volume
-    double dt, h;
-    long long step;
-    double band;
-    double tau;                  // occupancy threshold in the element type's terms
-    bool list_valid;             // list[cur] holds the first sweep's faces
-    int list_cur;                // which of the two lists is current
+    int* tile_seg;               // first segment of each tile of kFaceTile listed faces
+    int tile_cap;
+    long long step;              // index of the first step
+    double band;                 // FP64 plane-constant band (FP32 path)
+    double tau;                  // occupancy threshold
+    bool list_valid;             // list[list_cur] holds the first sweep's faces
+    int list_cur;
     cudaStream_t stream;
     long long* launches;
     Prof* prof;
     // learned normal (FP32 path only; null = MYC everywhere)
     const MlpBlob* mlp;
-    float4* net;                         // [K][N] network normal of each listed face's cell
-    int* tile_seg;                       // first segment of each tile of kFaceTile listed faces
-    int tile_cap;
-    float mlp_tol;                       // residual below which the network is kept outright
-    int* mlp_status;                     // set on a timed-out tensor-core wait
-    unsigned long long* mlp_counters;    // [0] faces on the network's normal, [1] on MYC's
+    float mlp_tol;                     // residual at or below which the network is kept outright
+    int* mlp_status;                   // set on a timed-out tensor-core wait
+    unsigned long long* mlp_counters;  // [0] faces on the network's normal, [1] on MYC's
+    // launch shape of the update pass (0 = default)
+    int update_warps;                  // warps per block
+    int update_blocks_per_sm;
 };
 
-template <typename T>
-__device__ __forceinline__ void gather_stencil(const T* __restrict__ cf, int x, const Dims& g, T st[27]) {
-    int i, j, k;
-    decode(x, g, i, j, k);
-    int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
-    int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
-    int km = k == 0 ? g.nz - 1 : k - 1, kp = k == g.nz - 1 ? 0 : k + 1;
-    const int is[3] = {im, i, ip}, js[3] = {jm, j, jp}, ks[3] = {km, k, kp};
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) st[c * 9 + b * 3 + a] = cf[cell(is[a], js[b], ks[c], g)];
-}
 
 // Face lists are segmented by block: block b of the listing kernels owns
 // list[b * cap .. b * cap + count[b]), filled through a shared-memory counter,
@@ -150,74 +129,6 @@ __global__ void __launch_bounds__(512) k_list_faces(const T* __restrict__ cin, c
     }
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) counts[blockIdx.x] = s_count;
-}
-
-// Flat index space over the segments: off[b] = first entry of segment b
-// (exclusive scan of the counts), off[nseg] = total.
-__device__ __forceinline__ int segment_of(const int* __restrict__ off, int nseg, int e) {
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Segment of entry e >= base given the segment sb of base: a short forward
-// walk (a tile of consecutive entries spans few segments).
-__device__ __forceinline__ int segment_from(const int* __restrict__ off, int sb, int e) {
-    while (off[sb + 1] <= e) ++sb;
-    return sb;
-}
-
-// Decoded listed face: field f, cell x of the face's high side, the cell
-// index t = f * N + x of its flux, the upwind donor cell.
-struct ListedFace {
-    int f, x, donor;
-    size_t t;
-};
-
-// uv receives the face velocity ud[x]; the donor is upwind of the face.
-template <typename T>
-__device__ __forceinline__ ListedFace decode_face(unsigned long long key, const Dims& g, int d,
-                                                  const T* __restrict__ ud, T& uv) {
-    ListedFace r;
-    r.f = (int)(key >> 54);
-    const int k = (int)((key >> 36) & 0x3ffffu);
-    const int j = (int)((key >> 18) & 0x3ffffu);
-    const int i = (int)(key & 0x3ffffu);
-    r.x = cell(i, j, k, g);
-    r.t = (size_t)r.f * g.N + r.x;
-    uv = ud[r.x];
-    r.donor = vsign(uv) > 0 ? step_cell(r.x, i, j, k, d, -1, g) : r.x;
-    return r;
-}
-
-// One thread per listed face, CTA-contiguous tiles of kFaceTile faces
-// (tile_seg gives each tile's first segment): MYC normal, plane constant
-// and PLIC flux of the donor.
-template <typename T>
-__global__ void __launch_bounds__(kFaceTile) k_face_flux(const T* __restrict__ cin, const T* __restrict__ ud,
-                                                         Dims g, int d, T sfac, T band,
-                                                         const unsigned long long* __restrict__ list,
-                                                         long long cap, const int* __restrict__ off, int nseg,
-                                                         const int* __restrict__ tile_seg, T* __restrict__ flux) {
-    const int n = off[nseg];
-    for (int base = blockIdx.x * kFaceTile; base < n; base += gridDim.x * kFaceTile) {
-        const int e = base + threadIdx.x;
-        if (e >= n) continue;
-        const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
-        T uv;
-        const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
-        const T s = uv * sfac;
-        T st[27];
-        gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
-        T m[3];
-        myc_normal(st, m);
-        const T alpha = plic_alpha_banded(m[0], m[1], m[2], st[13], band);
-        flux[fc.t] = face_flux(m, alpha, d, s);
-    }
 }
 
 template <typename T>
@@ -348,53 +259,90 @@ __global__ void __launch_bounds__(512, 2) k_update(const T* __restrict__ cin, T*
     if (threadIdx.x == 0 && threadIdx.y == 0) ncounts[blockIdx.x] = s_count;
 }
 
+// Rows of whole 16-byte lanes take the box kernels; others (a context only)
+// the scalar update and listing.
 template <typename T>
-cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
-    const Dims& g = a.g;
-    if (a.K == 0 || nsteps <= 0) return cudaSuccess;
-    const T sfac = (T)(a.dt / a.h);
-    const T band = (T)a.band;
-    const T tau = (T)a.tau;
-    const T* u = (const T*)a.u;
-    T* c = (T*)a.c;
-    T* b1 = (T*)a.buf1;
-    T* b2 = (T*)a.buf2;
-    T* fl = (T*)a.flux;
-    const long long words = (long long)g.rows * g.W;
-    // persistent-size grid: as many (32 x K)-thread blocks as fit on the
-    // SMs at 64 registers per thread, each walking a long range of words
-    const int per_sm = std::max(1, std::min(32, 32 / a.K));
-    // rows of whole 32-cell words take the vectorised update (16-byte lanes)
-    const bool vec = g.nx % 32 == 0;
-    int gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
+__host__ __device__ inline bool rows_vectorisable(const Dims& g) {
+    return g.nx % VecOf<T>::W == 0;
+}
+
+// Grid and per-block list capacity of one advance; every producer of a list
+// in it uses the same grid so that the consumers' segment walk is uniform.
+struct SweepGrid {
+    int gb, wpb;
+    long long cap;
+};
+
+template <typename T, int NB>
+SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
+    SweepGrid r;
     if (vec) {
-        // one resident wave of (32 x K)-thread blocks
-        int resident = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_update_vec<T>, 32 * a.K, 0) != cudaSuccess ||
-            resident < 1)
-            resident = per_sm;
-        gb = std::min(152 * resident, 2048);
+        constexpr int CH = 32 * VecOf<T>::W;
+        r.wpb = a.update_warps > 0 ? a.update_warps : 8;
+        int per_sm = a.update_blocks_per_sm;
+        if (per_sm <= 0 &&
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB>, 32 * r.wpb, 0) !=
+                 cudaSuccess ||
+             per_sm < 1))
+            per_sm = 1;
+        r.gb = std::max(1, std::min(152 * per_sm, kListBlocks / std::max(1, r.wpb / 8)));
+        r.gb = std::min(r.gb, (S.items + r.wpb - 1) / r.wpb);
+        r.gb = std::max(r.gb, 1);
+        const long long per_warp = ((long long)S.items + (long long)r.gb * r.wpb - 1) / ((long long)r.gb * r.wpb);
+        r.cap = 2LL * CH * r.wpb * per_warp;
+    } else {
+        const Dims& g = S.b[0].g;
+        const long long words = (long long)g.rows * g.W;
+        const int K = S.b[0].K;
+        const int per_sm = std::max(1, std::min(32, 32 / K));
+        r.wpb = K;
+        r.gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
+        r.cap = 2LL * 32 * K * ((words + r.gb - 1) / r.gb);
     }
-    // list segment per block: at most 2 faces per cell and field of the
-    // block's cells (words per block = ceil(words / gb); chunks of 32 * VW
-    // cells for the vectorised pass); gb * cap stays within the reserved span
-    long long cap = 2LL * 32 * a.K * ((words + gb - 1) / gb);
-    if (vec) {
-        const long long CH = 32LL * VecOf<T>::W, nch = ((long long)g.N + CH - 1) / CH;
-        cap = std::max(cap, 2LL * a.K * CH * ((nch + gb - 1) / gb));
+    return r;
+}
+
+template <typename T, int NB>
+void face_fluxes(const BoxSet<T, NB>& S, int d, int sweep, const unsigned long long* list, long long cap, int gb,
+                 SweepArgs& a) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.mlp) {
+            face_flux_learned_set<NB>(S, d, sweep, (float)a.band, list, cap, a.offsets, gb, a.tile_seg, a.mlp,
+                                      a.mlp_tol, a.mlp_status, a.mlp_counters, a.stream);
+            if (a.launches) *a.launches += 2;
+            return;
+        }
     }
-    // second list after the first list's reserved span (see the workspace layout)
-    unsigned long long* lists[2] = {a.list, a.list + (size_t)2 * 32 * a.Kcap * ((size_t)words + kSweepBlocks)};
+    k_face_flux_bx<T, NB><<<152 * 16, kFaceTile, 0, a.stream>>>(S, d, sweep, (T)a.band, list, cap, a.offsets, gb,
+                                                                 a.tile_seg);
+    if (a.launches) *a.launches += 1;
+}
+
+// nsteps steps of every box of S (Section 2.2 split advection with the
+// Weymouth & Yue term; c_c bits, clip and occupancy bits as in k_update).
+template <typename T, int NB>
+cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
+    if (S.n == 0 || nsteps <= 0) return cudaSuccess;
+    const bool vec = NB > 1 || rows_vectorisable<T>(S.b[0].g);
+    const SweepGrid G = sweep_grid(S, vec, a);
+    if ((long long)G.gb * G.cap > a.list_entries || G.gb > kSweepBlocks) return cudaErrorInvalidValue;
+    unsigned long long* lists[2] = {a.list, a.list + a.list_entries};
     int* counts[2] = {a.counts, a.counts + kSweepBlocks};
+    const T tau = (T)a.tau;
+    const BoxDev<T>& B0 = S.b[0];
+    const Dims& g0 = B0.g;
     for (int s = 0; s < nsteps; ++s) {
         const long long step = a.step + s;
         const int rot = (int)(step % 3);
-        const T* ins[3] = {c, b1, b2};
-        T* outs[3] = {b1, b2, c};
         if (!a.list_valid) {
             if (a.prof) a.prof->begin(P_FIND_FACES);
-            k_list_faces<T><<<gb, dim3(32, a.K), 0, a.stream>>>(c, u + (size_t)rot * g.N, g, rot, lists[a.list_cur],
-                                                                 cap, counts[a.list_cur]);
+            if (vec)
+                k_list_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, lists[a.list_cur], G.cap,
+                                                                    counts[a.list_cur]);
+            else
+                k_list_faces<T><<<G.gb, dim3(32, B0.K), 0, a.stream>>>(B0.c, B0.u + (size_t)rot * g0.N, g0, rot,
+                                                                        lists[a.list_cur], G.cap,
+                                                                        counts[a.list_cur]);
             if (a.prof) a.prof->end();
             if (a.launches) *a.launches += 1;
         }
@@ -402,40 +350,25 @@ cudaError_t advect_steps_t(AdvectArgs& a, int nsteps) {
             const int d = (rot + sw) % 3;
             // next sweep: within the step, or the first sweep of the next step
             const int dn = sw < 2 ? (rot + sw + 1) % 3 : (int)((step + 1) % 3);
-            const T* ud = u + (size_t)d * g.N;
-            const T* udn = u + (size_t)dn * g.N;
             const int cur = a.list_cur, nxt = 1 - a.list_cur;
             if (a.prof) a.prof->begin(P_FACE_FLUX);
-            scan_face_counts(counts[cur], a.offsets, gb, a.tile_seg, a.tile_cap, a.stream);
-            bool learned = false;
-            if constexpr (std::is_same<T, float>::value) {
-                if (a.mlp) {
-                    // network normals of the listed faces (tensor cores), then the judged fluxes
-                    learned = true;
-                    if (a.prof) { a.prof->end(); a.prof->begin(P_NET_NORMALS); }
-                    face_normals_net(ins[sw], ud, g, d, lists[cur], cap, a.offsets, gb, a.tile_seg, a.net,
-                                     a.mlp, a.mlp_status, a.stream);
-                    if (a.prof) { a.prof->end(); a.prof->begin(P_FACE_FLUX); }
-                    face_flux_judged(ins[sw], ud, g, d, sfac, band, lists[cur], cap, a.offsets, gb, a.tile_seg,
-                                     fl, a.net, a.mlp_tol, a.mlp_counters, a.stream);
-                    if (a.launches) *a.launches += 1;
-                }
-            }
-            if (!learned)
-                k_face_flux<T><<<152 * 16, kFaceTile, 0, a.stream>>>(ins[sw], ud, g, d, sfac, band, lists[cur],
-                                                                      cap, a.offsets, gb, a.tile_seg, fl);
+            scan_face_counts(counts[cur], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
+            if (a.launches) *a.launches += 1;
+            face_fluxes(S, d, sw, lists[cur], G.cap, G.gb, a);
             if (a.prof) { a.prof->end(); a.prof->begin(P_UPDATE); }
-            if (vec)
-                k_update_vec<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac,
-                                                                     tau, fl, a.ccbits, a.occbits, lists[nxt], cap,
-                                                                     counts[nxt], a.clipped);
-            else
-                k_update<T><<<gb, dim3(32, a.K), 0, a.stream>>>(ins[sw], outs[sw], ud, udn, g, d, dn, sw, sfac, tau,
-                                                                 fl, a.ccbits, a.occbits, lists[nxt], cap, counts[nxt],
-                                                                 a.clipped);
+            if (vec) {
+                k_update_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, d, dn, sw, tau, lists[nxt], G.cap,
+                                                                      counts[nxt]);
+            } else {
+                const T* ins[3] = {B0.c, B0.b1, B0.b2};
+                T* outs[3] = {B0.b1, B0.b2, B0.c};
+                k_update<T><<<G.gb, dim3(32, B0.K), 0, a.stream>>>(
+                    ins[sw], outs[sw], B0.u + (size_t)d * g0.N, B0.u + (size_t)dn * g0.N, g0, d, dn, sw, B0.sfac,
+                    tau, B0.flux, B0.ccbits, B0.occbits, lists[nxt], G.cap, counts[nxt], B0.clipped);
+            }
             if (a.prof) a.prof->end();
+            if (a.launches) *a.launches += 1;
             a.list_cur = nxt;
-            if (a.launches) *a.launches += 3;  // scan, flux, update
         }
         a.list_valid = true;
     }

@@ -91,9 +91,10 @@ bool config_valid(const vof_config* c) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Tiles of a face list at its largest (the list's reserved span).
-size_t tile_cap_for(size_t K, size_t words) {
-    return (2 * 32 * K * (words + (size_t)kSweepBlocks) + kFaceTile - 1) / kFaceTile;
+size_t list_entries_for(const vof_config* c) {
+    return (size_t)list_reserve(c->nx, c->ny, c->nz, c->k_capacity, c->precision == VOF_FP64 ? 8 : 4);
 }
+size_t tile_cap_for(const vof_config* c) { return (list_entries_for(c) + kFaceTile - 1) / kFaceTile; }
 
 Layout layout_for(const vof_config* c) {
     Layout L;
@@ -106,9 +107,8 @@ Layout layout_for(const vof_config* c) {
     L.size[S_BUF2] = K * N * es;
     L.size[S_FLUX] = K * N * es;
     // two face lists segmented by block; a segment holds up to 2 faces per
-    // cell and field of the block's row segments
-    // (any grid of gb <= kSweepBlocks blocks: gb * ceil(words / gb) <= words + gb)
-    L.size[S_LIST] = 2 * (2 * 32 * K * (words + (size_t)kSweepBlocks)) * 8;
+    // cell and field of the block's cells, for any grid the advance picks
+    L.size[S_LIST] = 2 * list_entries_for(c) * 8;
     L.size[S_COUNTS] = (3 * (size_t)kSweepBlocks + 1) * 4;
     L.size[S_MISC] = kMiscBytes;
     L.size[S_BITS] = K * words * 4;
@@ -136,7 +136,7 @@ Layout layout_for(const vof_config* c) {
     // network normal at the cell of every listed face (learned normal only)
     L.size[S_NET] = c->precision == VOF_MIXED_LEARNED ? K * N * 16 : 0;
     // first segment of each tile of kFaceTile entries of a face list
-    L.size[S_TILESEG] = (tile_cap_for(K, words) + 1) * 4;
+    L.size[S_TILESEG] = (tile_cap_for(c) + 1) * 4;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
         L.off[s] = o;
@@ -474,6 +474,36 @@ vof_status vof_set_velocity(vof_ctx* ctx, const void* u_dev) {
     return scan_velocity(ctx);
 }
 
+}  // extern "C"
+
+// The context's state as a one-box set.
+template <typename T>
+static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
+    BoxSet<T, 1> S;
+    BoxDev<T>& B = S.b[0];
+    const Dims& g = ctx->g;
+    const int CH = 32 * VecOf<T>::W;
+    B.g = g;
+    B.K = ctx->n_active;
+    B.item0 = 0;
+    B.cpr = (g.nx + CH - 1) / CH;
+    B.sfac = (T)(dt / ctx->cfg.h);
+    B.c = (T*)ctx->c;
+    B.b1 = ctx->slot<T>(S_BUF1);
+    B.b2 = ctx->slot<T>(S_BUF2);
+    B.flux = ctx->slot<T>(S_FLUX);
+    B.u = (const T*)ctx->u;
+    B.net = ctx->cfg.precision == VOF_MIXED_LEARNED ? ctx->slot<float4>(S_NET) : nullptr;
+    B.ccbits = ctx->slot<uint32_t>(S_CCBITS);
+    B.occbits = ctx->slot<uint32_t>(S_BITS);
+    B.clipped = clipped;
+    S.n = 1;
+    S.items = B.K * g.rows * B.cpr;
+    return S;
+}
+
+extern "C" {
+
 vof_status vof_set_mlp(vof_ctx* ctx, const void* weights_dev, double fallback_tol) {
     vof_status s = check_ctx(ctx);
     if (s != VOF_OK) return s;
@@ -497,47 +527,41 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
         VOF_CUDA(ctx, cudaMemsetAsync(clipped, 0, kMaxK * sizeof(double), ctx->stream));
         VOF_CUDA(ctx, cudaMemsetAsync(mlp_counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
     }
-    AdvectArgs a;
-    a.g = ctx->g;
-    a.c = ctx->c;
-    a.u = ctx->u;
-    a.buf1 = ctx->slot<void>(S_BUF1);
-    a.buf2 = ctx->slot<void>(S_BUF2);
-    a.flux = ctx->slot<void>(S_FLUX);
+    SweepArgs a;
     a.list = ctx->slot<unsigned long long>(S_LIST);
+    a.list_entries = (long long)list_entries_for(&ctx->cfg);
     a.counts = ctx->slot<int>(S_COUNTS);
     a.offsets = ctx->slot<int>(S_COUNTS) + 2 * kSweepBlocks;
-    a.Kcap = ctx->cfg.k_capacity;
-    a.ccbits = ctx->slot<uint32_t>(S_CCBITS);
-    a.occbits = ctx->slot<uint32_t>(S_BITS);
+    a.tile_seg = ctx->slot<int>(S_TILESEG);
+    a.tile_cap = (int)std::min<size_t>(tile_cap_for(&ctx->cfg), (size_t)INT32_MAX);
     a.tau = occupancy_tau(ctx);
     a.list_valid = false;
     a.list_cur = 0;
-    a.clipped = clipped;
-    a.dt = dt;
-    a.h = ctx->cfg.h;
     a.band = ctx->cfg.alpha_fp64_band;
     a.stream = ctx->stream;
     a.launches = &ctx->launches;
     a.prof = &ctx->prof;
     a.mlp = (const MlpBlob*)ctx->mlp;
-    a.net = ctx->slot<float4>(S_NET);
-    a.tile_seg = ctx->slot<int>(S_TILESEG);
-    a.tile_cap = (int)std::min<size_t>(tile_cap_for(ctx->cfg.k_capacity, (size_t)ctx->g.rows * ctx->g.W),
-                                       (size_t)INT32_MAX);
     a.mlp_tol = (float)ctx->mlp_tol;
     a.mlp_status = (int*)(ctx->misc() + kMiscMlpStatus);
     a.mlp_counters = mlp_counters;
+    a.update_warps = 0;
+    a.update_blocks_per_sm = 0;
     int moved_total = 0, fired_steps = 0;
     long long field_steps = 0;
     vof_status result = VOF_OK;
     int chunk = ctx->cfg.recolour ? 1 : nsteps;
     for (int done = 0; done < nsteps; done += chunk) {
         int n = std::min(chunk, nsteps - done);
-        a.K = ctx->n_active;
         a.step = ctx->step;
-        field_steps += (long long)a.K * n;
-        VOF_CUDA(ctx, ctx->fp64 ? advect_steps_fp64(a, n) : advect_steps_fp32(a, n));
+        field_steps += (long long)ctx->n_active * n;
+        if (ctx->fp64) {
+            const BoxSet<double, 1> S = ctx_box_set<double>(ctx, clipped, dt);
+            VOF_CUDA(ctx, advect_set_fp64(S, a, n));
+        } else {
+            const BoxSet<float, 1> S = ctx_box_set<float>(ctx, clipped, dt);
+            VOF_CUDA(ctx, advect_set_fp32(S, a, n));
+        }
         ctx->bits_valid = true;
         ctx->step += n;
         if (ctx->cfg.recolour) {

@@ -1,0 +1,360 @@
+// Split advection over a set of independent boxes (one box for a context,
+// up to kMaxBoxes for a batch): every pass of a sweep is one launch that
+// covers every field of every box.
+//
+// The set travels by value as a __grid_constant__ kernel parameter (about
+// 8 KB for 64 boxes; read in place from the parameter space), so a
+// captured CUDA graph holds it and no table has to be copied to the
+// device.  Work of the update and listing passes is split into items = one
+// 32 * VW-cell chunk of one row of one field of one box (VW cells per lane,
+// 16-byte accesses); items are numbered box by box, row chunk by row chunk,
+// field by field, and the grid walks them in bands of consecutive items so
+// that the fields of a chunk, and the neighbouring rows and planes of a
+// chunk, are read close together in time (L2 reuse of c and u).  The face
+// list of the next sweep holds 64-bit keys box | field | k | j | i.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "plic.cuh"
+#include "faces.cuh"
+#include "update_vec.cuh"
+
+namespace vof {
+
+template <typename T>
+struct BoxDev {
+    Dims g;
+    int K;      // fields advected
+    int item0;  // first work item of the box
+    int cpr;    // row chunks per row, ceil(nx / (32 VW))
+    T sfac;     // dt / h
+    T* c;       // [K][N] state (updated in place over a step)
+    T* b1;      // [K][N] state after the first sweep
+    T* b2;      // [K][N] state after the second sweep
+    T* flux;    // [K][N] flux of listed faces, at the face's high-side cell
+    const T* u; // [3][N] face velocities (low faces)
+    float4* net;        // [K][N] network normal at listed faces (learned path)
+    uint32_t* ccbits;   // [K][rows][W] c > 1/2 at the step start
+    uint32_t* occbits;  // [K][rows][W] c > tau after the step
+    double* clipped;    // [K] volume removed by the clip
+};
+
+// NB = capacity: 1 for a context, kMaxBoxes for a batch.
+template <typename T, int NB>
+struct BoxSet {
+    int n;
+    int items;
+    BoxDev<T> b[NB];
+};
+
+// Face-list key: box (6 bits) | field (4) | k | j | i (18 bits each).
+__device__ __forceinline__ unsigned long long box_face_key(int box, int f, int i, int j, int k) {
+    return ((unsigned long long)box << 58) | face_key(f, i, j, k);
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ int box_of_item(const BoxSet<T, NB>& S, int it) {
+    if (NB == 1) return 0;
+    int lo = 0, hi = S.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.b[mid].item0 <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* sweep_in(const BoxDev<T>& B, int sweep) {
+    return sweep == 0 ? B.c : (sweep == 1 ? B.b1 : B.b2);
+}
+template <typename T>
+__device__ __forceinline__ T* sweep_out(const BoxDev<T>& B, int sweep) {
+    return sweep == 0 ? B.b1 : (sweep == 1 ? B.b2 : B.c);
+}
+
+// Geometry of one item for lane `lane`.
+struct ItemCells {
+    int f, row, j, k, i0, x0;
+    bool valid;  // the lane's VW cells lie in the row
+    int lo_y, hi_y, lo_z, hi_z;
+};
+
+template <typename T>
+__device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, int lane) {
+    constexpr int VW = VecOf<T>::W;
+    const Dims& g = B.g;
+    ItemCells r;
+    const int chunk = local / B.K;
+    r.f = local - chunk * B.K;
+    r.row = chunk / B.cpr;
+    const int seg = chunk - r.row * B.cpr;
+    const int i0 = seg * 32 * VW + lane * VW;
+    r.valid = i0 < g.nx;
+    // lanes past the row's end work on the row's first cells (every index
+    // stays in the grid) and write nothing
+    r.i0 = r.valid ? i0 : 0;
+    r.x0 = r.row * g.nx + r.i0;
+    r.j = r.row % g.ny;
+    r.k = r.row / g.ny;
+    const int plane = g.nx * g.ny;
+    r.lo_y = r.j == 0 ? (g.ny - 1) * g.nx : -g.nx;
+    r.hi_y = r.j == g.ny - 1 ? -(g.ny - 1) * g.nx : g.nx;
+    r.lo_z = r.k == 0 ? (g.nz - 1) * plane : -plane;
+    r.hi_z = r.k == g.nz - 1 ? -(g.nz - 1) * plane : plane;
+    return r;
+}
+
+// Warp-aggregated append of nflag entries per lane to the block's segment;
+// returns the lane's first slot.
+__device__ __forceinline__ int warp_reserve(int nflag, int lane, int* s_count) {
+    int incl = nflag;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int wbase = 0;
+    if (lane == 31 && incl > 0) wbase = atomicAdd(s_count, incl);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    return wbase + incl - nflag;
+}
+
+// Faces of sweep d whose upwind donor is interfacial (start of a call, or
+// after a recolouring moved drops), from the state c of every box.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<T, NB> S, int d,
+                                                 unsigned long long* __restrict__ list, long long cap,
+                                                 int* __restrict__ counts) {
+    constexpr int VW = VecOf<T>::W;
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    unsigned long long* seg = list + (size_t)blockIdx.x * cap;
+    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < S.items; it += gridDim.x * wpb) {
+        const int bx = box_of_item(S, it);
+        const BoxDev<T>& B = S.b[bx];
+        const ItemCells ic = item_cells(B, it - B.item0, lane);
+        const T* cf = B.c + (size_t)ic.f * B.g.N;
+        const T* ud = B.u + (size_t)d * B.g.N;
+        T cx[VW], cl[VW], ul[VW];
+        ld16(cf + ic.x0, cx);
+        ld16(ud + ic.x0, ul);
+        if (d == 0) {
+            const T cprev = prev_along_x<T, VW>(cx, cf, ic.x0, ic.i0, B.g.nx, lane);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) cl[e] = e == 0 ? cprev : cx[e - 1];
+        } else {
+            ld16(cf + ic.x0 + (d == 1 ? ic.lo_y : ic.lo_z), cl);
+        }
+        uint32_t fl = 0;
+        int nflag = 0;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int sg = vsign(ul[e]);
+            const bool flag = ic.valid && sg != 0 && vclass(sg > 0 ? cl[e] : cx[e]) == 1;
+            fl |= (flag ? 1u : 0u) << e;
+            nflag += flag;
+        }
+        int pos = warp_reserve(nflag, lane, &s_count);
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+            if ((fl >> e) & 1u) seg[pos++] = box_face_key(bx, ic.f, ic.i0 + e, ic.j, ic.k);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
+}
+
+// Update pass of sweep `sweep` along d for every box (see k_update for the
+// arithmetic): c_out = c_in - (F_hi - F_lo) + c_c (s_hi - s_lo), c_c bits
+// written in sweep 0 and read after, the clip and the occupancy bits in
+// sweep 2, and the faces of the next sweep (direction dn) whose donor is
+// interfacial appended to the block's list segment.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSet<T, NB> S, int d, int dn,
+                                                   int sweep, T tau, unsigned long long* __restrict__ nlist,
+                                                   long long cap, int* __restrict__ ncounts) {
+    constexpr int VW = VecOf<T>::W;
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    unsigned long long* seg = nlist + (size_t)blockIdx.x * cap;
+    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < S.items; it += gridDim.x * wpb) {
+        const int bx = box_of_item(S, it);
+        const BoxDev<T>& B = S.b[bx];
+        const Dims& g = B.g;
+        const ItemCells ic = item_cells(B, it - B.item0, lane);
+        const int x0 = ic.x0, i0 = ic.i0, f = ic.f;
+        const size_t base = (size_t)f * g.N;
+        const T* __restrict__ cf = sweep_in(B, sweep) + base;
+        T* __restrict__ co = sweep_out(B, sweep) + base;
+        const T* __restrict__ ud = B.u + (size_t)d * g.N;
+        const T* __restrict__ udn = B.u + (size_t)dn * g.N;
+        const T* __restrict__ flux = B.flux;
+        const int hi_d = d == 1 ? ic.hi_y : ic.hi_z, lo_d = d == 1 ? ic.lo_y : ic.lo_z;
+        const int hi_dn = dn == 1 ? ic.hi_y : ic.hi_z;
+        T cx[VW], ulo[VW], uhi[VW], cl[VW], ch[VW], unl[VW], unh[VW];
+        ld16(cf + x0, cx);
+        ld16(ud + x0, ulo);
+        ld16(udn + x0, unl);
+        if (d == 0) {
+            const T cprev = prev_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
+            const T cnext = next_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
+            const T unext = next_along_x<T, VW>(ulo, ud, x0, i0, g.nx, lane);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                cl[e] = e == 0 ? cprev : cx[e - 1];
+                ch[e] = e == VW - 1 ? cnext : cx[e + 1];
+                uhi[e] = e == VW - 1 ? unext : ulo[e + 1];
+            }
+        } else {
+            ld16(cf + x0 + lo_d, cl);
+            ld16(cf + x0 + hi_d, ch);
+            ld16(ud + x0 + hi_d, uhi);
+        }
+        if (dn == 0) {
+            const T nnext = next_along_x<T, VW>(unl, udn, x0, i0, g.nx, lane);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) unh[e] = e == VW - 1 ? nnext : unl[e + 1];
+        } else {
+            ld16(udn + x0 + hi_dn, unh);
+        }
+        const size_t wpf = (size_t)g.rows * g.W;
+        const size_t word = (size_t)f * wpf + (size_t)ic.row * g.W + (i0 >> 5);
+        const int sh_bits = (lane * VW) & 31;
+        const bool leader = ic.valid && (lane & (32 / VW - 1)) == 0;
+        uint32_t ccm = 0;
+        if (sweep == 0) {
+            if (ic.valid) {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) ccm |= (above_half(cx[e]) ? 1u : 0u) << e;
+            }
+            const uint32_t w = gather_word<VW>(ccm, lane);
+            if (leader) B.ccbits[word] = w;
+        } else {
+            ccm = (B.ccbits[word] >> sh_bits) & ((1u << VW) - 1u);
+        }
+        T v[VW];
+        uint32_t occm = 0, flo = 0, fhi = 0;
+        int nflag = 0;
+        double removed = 0.0;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const int x = x0 + e;
+            const int sl = vsign(ulo[e]), sh = vsign(uhi[e]);
+            const int kl = sl == 0 ? 0 : vclass(sl > 0 ? cl[e] : cx[e]);
+            const int kh = sh == 0 ? 0 : vclass(sh < 0 ? ch[e] : cx[e]);
+            const bool cc = (ccm >> e) & 1u;
+            T ve;
+            if (kl == 0 && kh == 0 && !cc && is_exact_zero(cx[e])) {
+                ve = cx[e];
+            } else {
+                const int xh = d == 0 ? (e < VW - 1 ? x + 1 : (i0 + VW == g.nx ? x0 + VW - g.nx : x0 + VW))
+                                      : x + hi_d;
+                const T s_lo = ulo[e] * B.sfac, s_hi = uhi[e] * B.sfac;
+                const T F_lo = kl == 0 ? T(0) : (kl == 2 ? s_lo : flux[base + x]);
+                const T F_hi = kh == 0 ? T(0) : (kh == 2 ? s_hi : flux[base + xh]);
+                ve = cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi - s_lo);
+                if (sweep == 2 && (ve < T(0) || ve > T(1))) {
+                    const T cl0 = ve < T(0) ? T(0) : T(1);
+                    if (ic.valid) removed += (double)ve - (double)cl0;
+                    ve = cl0;
+                }
+            }
+            v[e] = ve;
+            if (ic.valid && sweep == 2 && ve > tau) occm |= 1u << e;
+            const bool interf = ic.valid && vclass(ve) == 1;
+            if (interf && vsign(unl[e]) < 0) {
+                flo |= 1u << e;
+                ++nflag;
+            }
+            if (interf && vsign(unh[e]) > 0) {
+                fhi |= 1u << e;
+                ++nflag;
+            }
+        }
+        if (ic.valid) st16(co + x0, v);
+        if (sweep == 2) {
+            const uint32_t w = gather_word<VW>(occm, lane);
+            if (leader) B.occbits[word] = w;
+            if (__any_sync(0xffffffffu, removed != 0.0)) {
+                for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+                if (lane == 0 && removed != 0.0) atomicAdd(B.clipped + f, removed);
+            }
+        }
+        int pos = warp_reserve(nflag, lane, &s_count);
+        if (nflag) {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const int i = i0 + e;
+                if ((flo >> e) & 1u) seg[pos++] = box_face_key(bx, f, i, ic.j, ic.k);
+                if ((fhi >> e) & 1u) {
+                    int ih = i, jh = ic.j, kh2 = ic.k;
+                    if (dn == 0) ih = i + 1 == g.nx ? 0 : i + 1;
+                    else if (dn == 1) jh = ic.j + 1 == g.ny ? 0 : ic.j + 1;
+                    else kh2 = ic.k + 1 == g.nz ? 0 : ic.k + 1;
+                    seg[pos++] = box_face_key(bx, f, ih, jh, kh2);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ncounts[blockIdx.x] = s_count;
+}
+
+// A listed face of a box set: box, field, the cell x of the face's high
+// side, the flux index t = f N + x, the upwind donor.
+struct BoxFace {
+    int box, f, x, donor;
+    size_t t;
+};
+
+template <typename T, int NB>
+__device__ __forceinline__ BoxFace decode_box_face(const BoxSet<T, NB>& S, unsigned long long key, int d, T& uv) {
+    BoxFace r;
+    r.box = (int)(key >> 58);
+    r.f = (int)((key >> 54) & 15u);
+    const int k = (int)((key >> 36) & 0x3ffffu);
+    const int j = (int)((key >> 18) & 0x3ffffu);
+    const int i = (int)(key & 0x3ffffu);
+    const Dims& g = S.b[r.box].g;
+    r.x = cell(i, j, k, g);
+    r.t = (size_t)r.f * g.N + r.x;
+    uv = S.b[r.box].u[(size_t)d * g.N + r.x];
+    r.donor = vsign(uv) > 0 ? step_cell(r.x, i, j, k, d, -1, g) : r.x;
+    return r;
+}
+
+// MYC fluxes of the listed faces of every box (one thread per face, tiles of
+// kFaceTile consecutive entries whose first segment tile_seg gives).
+template <typename T, int NB>
+__global__ void __launch_bounds__(kFaceTile) k_face_flux_bx(const __grid_constant__ BoxSet<T, NB> S, int d,
+                                                            int sweep, T band,
+                                                            const unsigned long long* __restrict__ list,
+                                                            long long cap, const int* __restrict__ off, int nseg,
+                                                            const int* __restrict__ tile_seg) {
+    const int n = off[nseg];
+    for (int base = blockIdx.x * kFaceTile; base < n; base += gridDim.x * kFaceTile) {
+        const int e = base + threadIdx.x;
+        if (e >= n) continue;
+        const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
+        T uv;
+        const BoxFace fc = decode_box_face(S, list[(size_t)sgi * cap + (e - off[sgi])], d, uv);
+        const BoxDev<T>& B = S.b[fc.box];
+        T st[27];
+        gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
+        T m[3];
+        myc_normal(st, m);
+        const T alpha = plic_alpha_banded(m[0], m[1], m[2], st[13], band);
+        B.flux[fc.t] = face_flux(m, alpha, d, uv * B.sfac);
+    }
+}
+
+}  // namespace vof

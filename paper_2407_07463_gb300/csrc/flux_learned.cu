@@ -12,7 +12,7 @@
 // that need MYC's normal and its residual are compacted to the first
 // threads of the CTA so that the fallback runs on full warps; then every
 // thread takes its plane constant and flux.
-#include "advect_impl.cuh"
+#include "boxes.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"
 
@@ -20,12 +20,11 @@ namespace vof {
 
 static_assert(kFaceTile == 128, "one face per thread of a 128-thread CTA");
 
-__global__ void __launch_bounds__(128, 3) k_face_normals_net(const float* __restrict__ cin,
-                                                             const float* __restrict__ ud, Dims g, int d,
-                                                             const unsigned long long* __restrict__ list,
+template <int NB>
+__global__ void __launch_bounds__(128, 4) k_face_normals_net(const __grid_constant__ BoxSet<float, NB> S, int d,
+                                                             int sweep, const unsigned long long* __restrict__ list,
                                                              long long cap, const int* __restrict__ off,
                                                              int nseg, const int* __restrict__ tile_seg,
-                                                             float4* __restrict__ net,
                                                              const MlpBlob* __restrict__ w,
                                                              int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -40,13 +39,14 @@ __global__ void __launch_bounds__(128, 3) k_face_normals_net(const float* __rest
         const int e = base + t;
         const bool valid = e < n;
         float st[27];
-        size_t fi = 0;
+        float4* dst = nullptr;
         if (valid) {
             const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
             float uv;
-            const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
-            fi = fc.t;
-            gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
+            const BoxFace fc = decode_box_face(S, list[(size_t)sgi * cap + (e - off[sgi])], d, uv);
+            const BoxDev<float>& B = S.b[fc.box];
+            dst = B.net + fc.t;
+            gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
         } else {
 #pragma unroll
             for (int q = 0; q < 27; ++q) st[q] = 0.5f;
@@ -61,19 +61,18 @@ __global__ void __launch_bounds__(128, 3) k_face_normals_net(const float* __rest
         if (valid) {
             float nn[3];
             canon_output(oc, fr, nn);
-            net[fi] = make_float4(nn[0], nn[1], nn[2], 0.f);
+            *dst = make_float4(nn[0], nn[1], nn[2], 0.f);
         }
     }
     mlp_cta_end(s, status);
 }
 
-__global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restrict__ cin,
-                                                          const float* __restrict__ ud, Dims g, int d, float sfac,
-                                                          float band, const unsigned long long* __restrict__ list,
+template <int NB>
+__global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant__ BoxSet<float, NB> S, int d,
+                                                          int sweep, float band,
+                                                          const unsigned long long* __restrict__ list,
                                                           long long cap, const int* __restrict__ off, int nseg,
-                                                          const int* __restrict__ tile_seg,
-                                                          float* __restrict__ flux,
-                                                          const float4* __restrict__ net, float tol,
+                                                          const int* __restrict__ tile_seg, float tol,
                                                           unsigned long long* __restrict__ counters) {
     __shared__ float s_st[27][128];  // stencil of thread t's donor in column t
     __shared__ float s_m[4][128];    // MYC's normal and plane constant where it replaces the network's
@@ -90,18 +89,19 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
         if (t == 0) s_nf = 0;
         float sv = 0.f, mn[3] = {1.f, 0.f, 0.f};
         bool net_ok = false;
-        size_t fi = 0;
+        float* dst = nullptr;
         if (valid) {
             const int sgi = segment_from(off, tile_seg[base / kFaceTile], e);
             float uv;
-            const ListedFace fc = decode_face(list[(size_t)sgi * cap + (e - off[sgi])], g, d, ud, uv);
-            sv = uv * sfac;
-            fi = fc.t;
+            const BoxFace fc = decode_box_face(S, list[(size_t)sgi * cap + (e - off[sgi])], d, uv);
+            const BoxDev<float>& B = S.b[fc.box];
+            sv = uv * B.sfac;
+            dst = B.flux + fc.t;
             float st[27];
-            gather_stencil(cin + (size_t)fc.f * g.N, fc.donor, g, st);
+            gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
 #pragma unroll
             for (int q = 0; q < 27; ++q) s_st[q][t] = st[q];
-            const float4 nv = net[fi];
+            const float4 nv = B.net[fc.t];
             const float nn[3] = {nv.x, nv.y, nv.z};
             net_ok = l1_normalise(nn, mn);
         }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
             // the residual's FP32 plane constant, refined in FP64 near c = 0 or 1
             const float cv = s_st[13][t];
             if (cv < band || cv > 1.f - band) al = plic_alpha_banded(m[0], m[1], m[2], cv, band);
-            flux[fi] = face_flux(m, al, d, sv);
+            *dst = face_flux(m, al, d, sv);
         }
         __syncthreads();  // the tile's shared arrays are reused by the next tile
     }
@@ -162,24 +162,26 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const float* __restric
     }
 }
 
-void face_flux_judged(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
-                      const unsigned long long* list, long long cap, const int* off, int nseg, const int* tile_seg,
-                      float* flux, const float4* net, float tol, unsigned long long* counters, cudaStream_t st) {
-    k_face_flux_judged<<<152 * 16, 128, 0, st>>>(cin, ud, g, d, sfac, band, list, cap, off, nseg, tile_seg, flux,
-                                                 net, tol, counters);
-}
-
-void face_normals_net(const float* cin, const float* ud, const Dims& g, int d, const unsigned long long* list,
-                      long long cap, const int* off, int nseg, const int* tile_seg, float4* net, const MlpBlob* w,
-                      int* status, cudaStream_t st) {
+template <int NB>
+void face_flux_learned_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
+                           long long cap, const int* off, int nseg, const int* tile_seg, const MlpBlob* w,
+                           float tol, int* status, unsigned long long* counters, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_face_normals_net, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_face_normals_net<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(MlpSmem));
         attr = true;
     }
-    k_face_normals_net<<<152 * 3, 128, sizeof(MlpSmem), st>>>(cin, ud, g, d, list, cap, off, nseg, tile_seg, net, w,
-                                                              status);
+    k_face_normals_net<NB><<<152 * 4, 128, sizeof(MlpSmem), st>>>(S, d, sweep, list, cap, off, nseg, tile_seg, w,
+                                                                  status);
+    k_face_flux_judged<NB><<<152 * 16, 128, 0, st>>>(S, d, sweep, band, list, cap, off, nseg, tile_seg, tol, counters);
 }
+
+template void face_flux_learned_set<1>(const BoxSet<float, 1>&, int, int, float, const unsigned long long*, long long,
+                                       const int*, int, const int*, const MlpBlob*, float, int*, unsigned long long*,
+                                       cudaStream_t);
+template void face_flux_learned_set<kMaxBoxes>(const BoxSet<float, kMaxBoxes>&, int, int, float,
+                                               const unsigned long long*, long long, const int*, int, const int*,
+                                               const MlpBlob*, float, int*, unsigned long long*, cudaStream_t);
 
 }  // namespace vof

@@ -55,20 +55,35 @@ constexpr int kMoveCap = 2048;        // moving drops per recolour call
 constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
 constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a sweep
 
-struct AdvectArgs;
+struct SweepArgs;
 struct MlpBlob;
-// Network normal of the donor of every listed face of one sweep (FP32
-// path): net[f * N + x] for the face at cell x of field f.
-void face_normals_net(const float* cin, const float* ud, const Dims& g, int d, const unsigned long long* list,
-                      long long cap, const int* off, int nseg, const int* tile_seg, float4* net, const MlpBlob* w,
-                      int* status, cudaStream_t st);
-// Fluxes of the listed faces with the judged learned normal (network normal
-// net[f * N + x] against MYC's), counters[0/1] += faces on network / MYC.
-void face_flux_judged(const float* cin, const float* ud, const Dims& g, int d, float sfac, float band,
-                      const unsigned long long* list, long long cap, const int* off, int nseg, const int* tile_seg,
-                      float* flux, const float4* net, float tol, unsigned long long* counters, cudaStream_t st);
-cudaError_t advect_steps_fp64(AdvectArgs& a, int nsteps);
-cudaError_t advect_steps_fp32(AdvectArgs& a, int nsteps);
+template <typename T, int NB>
+struct BoxSet;
+constexpr int kMaxBoxes = 64;
+// Largest grid of the list-producing passes.
+constexpr int kListBlocks = 2048;
+// Network normals, then judged fluxes, of the listed faces of one sweep of
+// a box set (FP32 path with the learned normal); counters[0/1] += faces on
+// the network's / MYC's normal.
+template <int NB>
+void face_flux_learned_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
+                           long long cap, const int* off, int nseg, const int* tile_seg, const MlpBlob* w,
+                           float tol, int* status, unsigned long long* counters, cudaStream_t st);
+// nsteps steps of every box of a set (one box: a context; up to kMaxBoxes:
+// a batch).
+cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps);
+cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps);
+cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps);
+cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps);
+// Face-list entries to reserve per list for K fields of grid g (either
+// sweep path, any launch shape the advance may choose).
+inline long long list_reserve(int nx, int ny, int nz, int K, int es) {
+    const long long rows = (long long)ny * nz, words = rows * ((nx + 31) / 32);
+    const long long scalar = 2LL * 32 * K * (words + kSweepBlocks);
+    const long long CH = 512 / es, cpr = (nx + CH - 1) / CH;
+    const long long vec = 2LL * CH * ((long long)K * rows * cpr + 8LL * kListBlocks);
+    return scalar > vec ? scalar : vec;
+}
 
 // Exclusive scan of n ints (one block); off[n] = total.
 cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st);

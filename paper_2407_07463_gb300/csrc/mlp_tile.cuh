@@ -18,12 +18,13 @@ namespace vof {
 // Shared-memory image of the network plus activation tiles.
 // H holds the layer-1 input (128 x 64, hi | lo) at its start, then each
 // hidden activation tile (128 x 128, hi | lo) once the layer reading the
-// previous content has completed.
+// previous content has completed.  The weights are held once: the MMA
+// chain over the hi and lo halves of K reads the same weight columns.
 struct MlpSmem {
-    unsigned char H[128 * kHidHL * 2];     // 128 x 128
-    unsigned char W1[kHid * kInHL * 2];    // 64 x 64 (W1 | W1)
-    unsigned char W2[kHid * kHidHL * 2];   // 64 x 128 (W2 | W2)
-    unsigned char W3[kOutP * kHidHL * 2];  // 16 x 128 (W3 | W3)
+    unsigned char H[128 * kHidHL * 2];   // 128 x 128
+    unsigned char W1[kHid * kIn * 2];    // 64 x 32
+    unsigned char W2[kHid * kHid * 2];   // 64 x 64
+    unsigned char W3[kOutP * kHid * 2];  // 16 x 64
     float b1[kHid], b2[kHid], b3[kOutP];
     uint64_t bar;
     uint32_t tbase;
@@ -31,9 +32,12 @@ struct MlpSmem {
 };
 
 __device__ __forceinline__ void load_weights(MlpSmem& s, const MlpBlob* __restrict__ w) {
-    load_weight_pair(s.W1, w->W1, kHid, kIn, threadIdx.x, blockDim.x);
-    load_weight_pair(s.W2, w->W2, kHid, kHid, threadIdx.x, blockDim.x);
-    load_weight_pair(s.W3, w->W3, kOutP, kHid, threadIdx.x, blockDim.x);
+    for (int idx = threadIdx.x; idx < kHid * kIn; idx += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(s.W1 + tc::kmajor_offset(idx / kIn, idx % kIn, kIn)) = w->W1[idx];
+    for (int idx = threadIdx.x; idx < kHid * kHid; idx += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(s.W2 + tc::kmajor_offset(idx / kHid, idx % kHid, kHid)) = w->W2[idx];
+    for (int idx = threadIdx.x; idx < kOutP * kHid; idx += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(s.W3 + tc::kmajor_offset(idx / kHid, idx % kHid, kHid)) = w->W3[idx];
     for (int idx = threadIdx.x; idx < kHid; idx += blockDim.x) {
         s.b1[idx] = w->b1[idx];
         s.b2[idx] = w->b2[idx];
@@ -48,16 +52,19 @@ __device__ __forceinline__ void store_input_row(MlpSmem& s, int t, const float x
 
 // Tensor-memory columns of the three layer outputs.
 // D3 reuses D1's columns (D1 is in shared memory before layer 2 is issued),
-// so four CTAs would fit the 512 columns of an SM.
+// so four CTAs fit the 512 columns of an SM.
 constexpr uint32_t kColD1 = 0, kColD2 = 64, kColD3 = 0, kTmemCols = 128;
 
-// Issue one layer (thread 0): D = A * W^T over K in steps of 16.
-__device__ __forceinline__ void issue_layer(uint32_t d, const unsigned char* A, const unsigned char* W, int K, int N,
-                                            uint64_t* bar) {
+// Issue one layer (thread 0): D = [A_hi | A_lo] * [W | W]^T, i.e. the K
+// steps of 16 run over the KA = 2 KW columns of A while the weight
+// descriptor wraps around W's KW columns.
+__device__ __forceinline__ void issue_layer(uint32_t d, const unsigned char* A, int KA, const unsigned char* W, int KW,
+                                            int N, uint64_t* bar) {
     const uint32_t idesc = tc::idesc_bf16(128, N);
-    for (int s = 0; s < K / 16; ++s)
-        tc::mma_bf16(d, tc::sdesc(tc::smem_u32(A) + s * 256, K), tc::sdesc(tc::smem_u32(W) + s * 256, K), idesc,
-                     s > 0);
+    const int ws = KW / 16;
+    for (int s = 0; s < KA / 16; ++s)
+        tc::mma_bf16(d, tc::sdesc(tc::smem_u32(A) + s * 256, KA), tc::sdesc(tc::smem_u32(W) + (s % ws) * 256, KW),
+                     idesc, s > 0);
     tc::mma_commit(bar);
 }
 
@@ -86,7 +93,7 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD1, s.H, s.W1, kInHL, kHid, &s.bar);
+    if (t == 0) issue_layer(taddr + kColD1, s.H, kInHL, s.W1, kIn, kHid, &s.bar);
     if (!finish_layer(s, phase)) return false;
     for (int c0 = 0; c0 < kHid; c0 += 16) {
         float v[16];
@@ -97,7 +104,7 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD2, s.H, s.W2, kHidHL, kHid, &s.bar);
+    if (t == 0) issue_layer(taddr + kColD2, s.H, kHidHL, s.W2, kHid, kHid, &s.bar);
     if (!finish_layer(s, phase)) return false;
     float h2[kHid];
     for (int c0 = 0; c0 < kHid; c0 += 16) {
@@ -111,7 +118,7 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (t == 0) issue_layer(taddr + kColD3, s.H, s.W3, kHidHL, kOutP, &s.bar);
+    if (t == 0) issue_layer(taddr + kColD3, s.H, kHidHL, s.W3, kHid, kOutP, &s.bar);
     if (!finish_layer(s, phase)) return false;
     float v[16];
     tc::tmem_ld16(taddr + lane_off + kColD3, v);
