@@ -356,7 +356,75 @@ vof_status vof_profile_enable(vof_ctx *ctx, int32_t enable);
 vof_status vof_profile_read(vof_ctx *ctx, int64_t *launches, double *ms, int32_t n);
 const char *vof_profile_class_name(int32_t cls);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent boxes (no counterpart in the paper, which
+ * advances one box).  Every box follows the arithmetic of vof_step without
+ * recolouring: the Section 2.2 split advection of each active field, the
+ * Weymouth-Yue term, the clip after the third sweep and the occupancy bits.
+ * Each pass of a sweep is one launch covering every field of every box; a
+ * step is replayed from a captured CUDA graph (one graph per sweep rotation
+ * and list parity, captured on first use); the launch shape of the update
+ * pass (warps per block, resident blocks per SM) is chosen by timing the
+ * candidates on the batch's own first sweep (vof_batch_tune, run by the
+ * first vof_batch_step when cfg.autotune is set).  The library allocates
+ * nothing: the caller passes one device workspace.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t nx, ny, nz;  /* cells; nx a multiple of 4 (FP32) or 2 (FP64) */
+    int32_t k_capacity;  /* fields stored in c_dev, 1..16 */
+    int32_t k_active;    /* fields advected, 1..k_capacity */
+    void *c_dev;         /* [k_capacity][nz][ny][nx], 16-byte aligned, updated in place */
+    const void *u_dev;   /* [3][nz][ny][nx] low-face velocities, 16-byte aligned */
+    double dt;           /* time step of this box; max |u| dt / h <= 1/2 */
+} vof_box_desc;
+
+typedef struct {
+    int32_t precision;       /* vof_precision, the same for every box */
+    double h;                /* cell size of every box */
+    double tag_tau;          /* occupancy threshold of the bits (default 1e-6) */
+    double alpha_fp64_band;  /* as in vof_config (FP32 paths) */
+    int32_t use_graph;       /* 1: replay captured graphs (default 1) */
+    int32_t autotune;        /* 1: tune the update launch shape (default 1) */
+} vof_batch_config;
+
+typedef struct {
+    int64_t steps_done;
+    int32_t n_boxes;
+    int64_t cell_fields_per_step;  /* sum over boxes of cells x active fields */
+    double clipped_volume[64];     /* per box, accumulated since init */
+    int64_t faces_network, faces_myc; /* VOF_MIXED_LEARNED, accumulated */
+    int32_t update_warps, update_blocks_per_sm; /* launch shape in use */
+    int32_t tune_candidates;       /* shapes timed by the tuner (0: not tuned) */
+    float tune_best_ms;            /* median first-sweep time of the chosen shape */
+    int64_t graph_launches, direct_steps;
+} vof_batch_report_t;
+
+typedef struct vof_batch vof_batch;
+
+vof_status vof_batch_config_default(vof_batch_config *cfg);
+/* Bytes of workspace for the batch; 0 for an invalid config or box (see
+ * vof_box_desc), or n_boxes outside 1..64. */
+size_t vof_batch_workspace_size(const vof_batch_config *cfg, const vof_box_desc *boxes, int32_t n_boxes);
+/* Borrows the boxes' c and u and the workspace (256-byte aligned) until
+ * vof_batch_destroy.  Scans every velocity: VOF_ERR_NONFINITE, VOF_ERR_CFL
+ * (max |u| dt / h > 1/2 in some box), VOF_ERR_WORKSPACE, VOF_ERR_ARG. */
+vof_status vof_batch_init(const vof_batch_config *cfg, const vof_box_desc *boxes, int32_t n_boxes,
+                          void *workspace_dev, size_t workspace_bytes, void *stream, vof_batch **out);
+/* Learned normal for a VOF_MIXED_LEARNED batch (as vof_set_mlp). */
+vof_status vof_batch_set_mlp(vof_batch *batch, const void *weights_dev, double fallback_tol);
+/* Times the update launch shapes on the batch's first sweep (the state is
+ * not modified) and keeps the fastest. */
+vof_status vof_batch_tune(vof_batch *batch);
+/* nsteps steps of every box, asynchronous on the batch's stream. */
+vof_status vof_batch_step(vof_batch *batch, int32_t nsteps);
+/* Synchronises; VOF_ERR_TIMEOUT if a tensor-core wait gave up. */
+vof_status vof_batch_report(vof_batch *batch, vof_batch_report_t *report);
+void vof_batch_destroy(vof_batch *batch);
+
 const char *vof_status_string(vof_status s);
+/* Name of the last CUDA error a call of this thread met and reported as
+ * VOF_ERR_CUDA ("no error" if none). */
+const char *vof_last_cuda_error(void);
 void vof_destroy(vof_ctx *ctx);
 
 #ifdef __cplusplus

@@ -8,4 +8,7 @@ cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps)
 cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps) {
     return advect_set(S, a, nsteps);
 }
+cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a) {
+    return advect_first_sweep(S, a);
+}
 }  // namespace vof

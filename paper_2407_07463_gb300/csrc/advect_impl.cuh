@@ -375,4 +375,24 @@ cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
     return cudaGetLastError();
 }
 
+// Listing from c and the first sweep of step a.step only (c -> first
+// scratch buffer; c itself is not modified): a representative, repeatable
+// unit of work for timing launch shapes.
+template <typename T, int NB>
+cudaError_t advect_first_sweep(const BoxSet<T, NB>& S, SweepArgs& a) {
+    if (S.n == 0) return cudaSuccess;
+    const bool vec = NB > 1 || rows_vectorisable<T>(S.b[0].g);
+    if (!vec) return cudaErrorInvalidValue;
+    const SweepGrid G = sweep_grid(S, vec, a);
+    if ((long long)G.gb * G.cap > a.list_entries || G.gb > kSweepBlocks) return cudaErrorInvalidValue;
+    unsigned long long* lists[2] = {a.list, a.list + a.list_entries};
+    int* counts[2] = {a.counts, a.counts + kSweepBlocks};
+    const int rot = (int)(a.step % 3), dn = (rot + 1) % 3;
+    k_list_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, lists[0], G.cap, counts[0]);
+    scan_face_counts(counts[0], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
+    face_fluxes(S, rot, 0, lists[0], G.cap, G.gb, a);
+    k_update_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, dn, 0, (T)a.tau, lists[1], G.cap, counts[1]);
+    return cudaGetLastError();
+}
+
 }  // namespace vof

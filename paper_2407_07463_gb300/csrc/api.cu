@@ -183,7 +183,9 @@ vof_status cuda_fail(vof_ctx* ctx) {
 
 #define VOF_CUDA(ctx, expr)                       \
     do {                                          \
-        if ((expr) != cudaSuccess) {              \
+        const cudaError_t e_ = (expr);            \
+        if (e_ != cudaSuccess) {                  \
+            note_cuda_error(e_);                  \
             (void)cudaGetLastError();             \
             return cuda_fail(ctx);                \
         }                                         \
@@ -922,6 +924,8 @@ vof_status vof_profile_read(vof_ctx* ctx, int64_t* launches, double* ms, int32_t
     p.n = 0;
     return VOF_OK;
 }
+
+const char* vof_last_cuda_error(void) { return vof::last_cuda_error_name(); }
 
 const char* vof_profile_class_name(int32_t cls) {
     static const char* names[P_COUNT] = {"list_faces", "face_flux", "update", "pack_bits", "near_contact",

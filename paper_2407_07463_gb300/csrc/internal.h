@@ -55,6 +55,10 @@ constexpr int kMoveCap = 2048;        // moving drops per recolour call
 constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
 constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a sweep
 
+// Keeps the name of the last CUDA error a library call met (for
+// vof_last_cuda_error); returns the error unchanged.
+cudaError_t note_cuda_error(cudaError_t e);
+const char* last_cuda_error_name();
 struct SweepArgs;
 struct MlpBlob;
 template <typename T, int NB>
@@ -75,6 +79,9 @@ cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps
 cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps);
+// Listing and first sweep of a batch only (state untouched; for timing).
+cudaError_t advect_first_sweep_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a);
+cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a);
 // Face-list entries to reserve per list for K fields of grid g (either
 // sweep path, any launch shape the advance may choose).
 inline long long list_reserve(int nx, int ny, int nz, int K, int es) {

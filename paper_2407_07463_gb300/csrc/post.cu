@@ -425,4 +425,15 @@ cudaError_t velocity_scan(bool fp64, const void* u, long long n, double* out2, c
     return cudaGetLastError();
 }
 
+namespace {
+thread_local const char* g_last_cuda_error = "no error";
+}
+
+cudaError_t note_cuda_error(cudaError_t e) {
+    if (e != cudaSuccess) g_last_cuda_error = cudaGetErrorName(e);
+    return e;
+}
+
+const char* last_cuda_error_name() { return g_last_cuda_error; }
+
 }  // namespace vof

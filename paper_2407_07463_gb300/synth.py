@@ -377,3 +377,28 @@ def config_large(seed=3, k_capacity=8):
     return make_workload("256^3 K=8 phi=0.3 r=8", n=256, k_capacity=k_capacity, phi=0.3,
                          radius=8.0, n_modes=16, amplitude=0.5, drift=1.0, cfl=0.3,
                          steps=100, seed=seed)
+
+
+def config_batched(seed=5, n_boxes=64, sizes=(32, 48, 64, 96, 128)):
+    """Independent tri-periodic boxes: edge drawn from ``sizes``, phi uniform
+    in [0.05, 0.3], K uniform in [2, 8] (raised to the number of fields the
+    initial colouring needs), spheres of radius 4 cells in boxes under 64
+    cells and 8 cells otherwise, 16-mode solenoidal velocity of amplitude 0.5
+    plus a vertical drift of 1, CFL 0.3.  Returns a list of Workloads."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n_boxes):
+        n = int(rng.choice(sizes))
+        phi = float(rng.uniform(0.05, 0.3))
+        k = int(rng.integers(2, 9))
+        r = 4.0 if n < 64 else 8.0
+        shape = (n, n, n)
+        ns = n_spheres_for_phi(shape, r, phi)
+        centres = rsa_centres(shape, r, ns, seed * 1000 + b)
+        colours, used = greedy_colours(shape, centres, r, 2)
+        K = max(k, int(used))
+        c = coloured_fields(shape, centres, r, colours, K)
+        u = solenoidal_velocity(shape, 16, 0.5, 1.0, seed * 1000 + b + 500)
+        out.append(Workload(f"box {b}: {n}^3 K={K} phi={phi:.3f} r={r:g}", shape, K, int(used), c, u,
+                            dt_for_cfl(u, 0.3), 1.0, 1, r, centres, colours))
+    return out

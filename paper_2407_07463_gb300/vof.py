@@ -27,7 +27,10 @@ STATUS = {0: "VOF_OK", -1: "VOF_ERR_ARG", -2: "VOF_ERR_CUDA", -3: "VOF_ERR_WORKS
 class VofError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        extra = ""
+        if status == -2 and _lib is not None:
+            extra = f" ({_lib.vof_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {STATUS.get(status, status)}{extra}")
 
 
 class vof_config(C.Structure):
@@ -44,6 +47,24 @@ class vof_step_report(C.Structure):
                 ("n_active", C.c_int32), ("n_moved", C.c_int32),
                 ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64),
                 ("faces_network", C.c_int64), ("faces_myc", C.c_int64)]
+
+
+class vof_box_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("k_capacity", C.c_int32),
+                ("k_active", C.c_int32), ("c_dev", C.c_void_p), ("u_dev", C.c_void_p), ("dt", C.c_double)]
+
+
+class vof_batch_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("h", C.c_double), ("tag_tau", C.c_double),
+                ("alpha_fp64_band", C.c_double), ("use_graph", C.c_int32), ("autotune", C.c_int32)]
+
+
+class vof_batch_report_t(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("n_boxes", C.c_int32), ("cell_fields_per_step", C.c_int64),
+                ("clipped_volume", C.c_double * 64), ("faces_network", C.c_int64), ("faces_myc", C.c_int64),
+                ("update_warps", C.c_int32), ("update_blocks_per_sm", C.c_int32),
+                ("tune_candidates", C.c_int32), ("tune_best_ms", C.c_float), ("graph_launches", C.c_int64),
+                ("direct_steps", C.c_int64)]
 
 
 class vof_train_params(C.Structure):
@@ -76,7 +97,10 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_profile_class_name", "vof_label_noalloc", "vof_mlp_weights_size",
            "vof_mlp_forward", "vof_tc_gemm_check", "vof_mlp_train_params_default",
            "vof_mlp_train_workspace_size", "vof_mlp_train", "vof_mlp_grad",
-           "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals"]
+           "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals",
+           "vof_batch_config_default", "vof_batch_workspace_size", "vof_batch_init", "vof_batch_set_mlp",
+           "vof_batch_tune", "vof_batch_step", "vof_batch_report", "vof_batch_destroy",
+           "vof_last_cuda_error"]
 
 
 def lib():
@@ -125,6 +149,16 @@ def lib():
         "vof_mlp_params_to_weights": (C.c_int, [vp, vp, vp]),
         "vof_set_mlp": (C.c_int, [vp, vp, dbl]),
         "vof_learned_normals": (C.c_int, [vp, vp, i64, dbl, vp, vp, vp]),
+        "vof_batch_config_default": (C.c_int, [C.POINTER(vof_batch_config)]),
+        "vof_batch_workspace_size": (C.c_size_t, [C.POINTER(vof_batch_config), C.POINTER(vof_box_desc), i32]),
+        "vof_batch_init": (C.c_int, [C.POINTER(vof_batch_config), C.POINTER(vof_box_desc), i32, vp, C.c_size_t,
+                                     vp, C.POINTER(vp)]),
+        "vof_batch_set_mlp": (C.c_int, [vp, vp, dbl]),
+        "vof_batch_tune": (C.c_int, [vp]),
+        "vof_batch_step": (C.c_int, [vp, i32]),
+        "vof_batch_report": (C.c_int, [vp, C.POINTER(vof_batch_report_t)]),
+        "vof_batch_destroy": (None, [vp]),
+        "vof_last_cuda_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -446,3 +480,75 @@ class Context:
     @property
     def launches(self):
         return int(lib().vof_launch_count(self.handle))
+
+
+# --------------------------------------------------------------------------- batches
+
+
+class Batch:
+    """Independent boxes advanced together (one launch per sweep pass for
+    every box, graph replay, tuned update launch shape).  boxes: list of
+    (c, u, dt) with c [K][nz][ny][nx] and u [3][nz][ny][nx] device tensors
+    of the precision's dtype; k_active: list or None (all fields)."""
+
+    def __init__(self, boxes, precision=VOF_MIXED, k_active=None, h=1.0, tag_tau=1e-6, band=1e-3,
+                 use_graph=True, autotune=True, stream=None):
+        import torch
+        cfg = vof_batch_config()
+        _check(lib().vof_batch_config_default(C.byref(cfg)), "vof_batch_config_default")
+        cfg.precision = precision
+        cfg.h = h
+        cfg.tag_tau = tag_tau
+        cfg.alpha_fp64_band = band
+        cfg.use_graph = 1 if use_graph else 0
+        cfg.autotune = 1 if autotune else 0
+        self.cfg = cfg
+        self.boxes = boxes
+        n = len(boxes)
+        arr = (vof_box_desc * n)()
+        for b, (c, u, dt) in enumerate(boxes):
+            K, nz, ny, nx = c.shape
+            arr[b].nx, arr[b].ny, arr[b].nz = nx, ny, nz
+            arr[b].k_capacity = K
+            arr[b].k_active = K if k_active is None else int(k_active[b])
+            arr[b].c_dev = _ptr(c)
+            arr[b].u_dev = _ptr(u)
+            arr[b].dt = float(dt)
+        self.desc = arr
+        nbytes = int(lib().vof_batch_workspace_size(C.byref(cfg), arr, n))
+        if nbytes == 0:
+            raise VofError(VOF_ERR_ARG, "vof_batch_workspace_size")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=boxes[0][0].device)
+        h_ = C.c_void_p()
+        _check(lib().vof_batch_init(C.byref(cfg), arr, n, _ptr(self.workspace), nbytes, _stream(self.stream),
+                                    C.byref(h_)), "vof_batch_init")
+        self.handle = h_
+
+    def set_mlp(self, weights, fallback_tol=1e-3):
+        self.mlp_weights = weights
+        _check(lib().vof_batch_set_mlp(self.handle, _ptr(weights), float(fallback_tol)), "vof_batch_set_mlp")
+
+    def tune(self):
+        _check(lib().vof_batch_tune(self.handle), "vof_batch_tune")
+
+    def step(self, nsteps=1):
+        _check(lib().vof_batch_step(self.handle, int(nsteps)), "vof_batch_step")
+
+    def report(self):
+        r = vof_batch_report_t()
+        _check(lib().vof_batch_report(self.handle, C.byref(r)), "vof_batch_report")
+        d = {k: getattr(r, k) for k, _ in vof_batch_report_t._fields_ if k != "clipped_volume"}
+        d["clipped_volume"] = list(r.clipped_volume[:r.n_boxes])
+        return d
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().vof_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
