@@ -174,6 +174,61 @@ def algorithmic_bytes(cls, n_cells, fields, es):
     return None
 
 
+# FP32 operations per listed face of the judged learned flux (counted from
+# the kernel's formulation: the branch-free volume takes about 57 operations
+# per cell, a plane constant about 100): the network normal's 27-cell
+# residual with its plane constant, the plane's flux; for the faces above the
+# tolerance also MYC's normal and residual.
+RESIDUAL_FLOPS = 27 * 57 + 100
+MYC_FLOPS = 120
+FLUX_FLOPS = 60
+# multiply-adds of the network per stencil (27-64-64-3), as algorithmic work
+MLP_FLOPS = 2 * (27 * 64 + 64 * 64 + 64 * 3)
+
+
+def bf16_peak():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s"
+
+
+def class_roofline(name, cnt, tot_ms, n_cells, fields, es, rep, learned, hbm, peak_src, sm_mhz, args):
+    """Roofline entry of one kernel class from its live CUDA-event time."""
+    avg_s = tot_ms / cnt * 1e-3
+    faces = (rep.get("faces_network", 0) or 0) + (rep.get("faces_myc", 0) or 0)
+    if name == "update":
+        alg = algorithmic_bytes(name, n_cells, fields, es)
+        ach = alg / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    if name == "face_flux" and learned and faces:
+        per_launch = faces / cnt
+        judged = (rep.get("faces_myc_judged", 0) or 0) / cnt
+        flops = per_launch * (RESIDUAL_FLOPS + FLUX_FLOPS) + judged * (MYC_FLOPS + RESIDUAL_FLOPS)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / avg_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "algorithmic_flops_per_launch": flops,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock)"}
+    if name == "net_normals" and faces:
+        flops = faces / cnt * MLP_FLOPS
+        pk, src = bf16_peak()
+        ach = flops / avg_s / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "algorithmic_flops_per_launch": flops, "peak_source": src}
+    if name in ("list_faces", "pack_bits", "near_contact"):
+        alg = algorithmic_bytes(name, n_cells, fields, es)
+        if alg is None:
+            return None
+        ach = alg / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+    return None
+
+
 def step_bytes(n_cells, fields, es):
     """The method's own minimum per step (read and write c once per step,
     the three velocity components once)."""
@@ -388,31 +443,33 @@ def run_ours(args, rank, world):
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (and the update pass's HBM one)
     hbm, peak_src = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     roof = None
-    if dom:
-        name, (cnt, tot) = dom
-        fields = rep["field_steps"] / max(args.steps, 1)
-        alg = algorithmic_bytes(name, N, fields, es)
-        traffic = None
-        try:
-            with open(TRAFFIC) as f:
-                tr = json.load(f)
-            if tr.get("source_hash") == src_hash() and name in tr.get("kernels", {}):
-                traffic = tr["kernels"][name]
-        except (OSError, ValueError):
-            pass
-        if alg is not None:
-            ach = alg / (tot / cnt * 1e-3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": traffic, "kernel": name, "launches": cnt,
-                    "avg_ms": tot / cnt, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src,
-                    "share_of_timed": tot / ms}
-        else:
-            roof = {"bound": "alu", "kernel": name, "launches": cnt, "avg_ms": tot / cnt,
-                    "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": traffic}
+    roof_update = None
+    fields = rep["field_steps"] / max(args.steps, 1)
+    traffic_tab = {}
+    try:
+        with open(TRAFFIC) as f:
+            tr = json.load(f)
+        if tr.get("source_hash") == src_hash():
+            traffic_tab = tr.get("kernels", {})
+    except (OSError, ValueError):
+        pass
+    for name, (cnt, tot) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        r = class_roofline(name, cnt, tot, N, fields, es, rep, prec == vof.VOF_MIXED_LEARNED, hbm, peak_src,
+                           sm_mhz, args)
+        if r is None:
+            continue
+        r.update({"kernel": name, "launches": cnt, "avg_ms": tot / cnt, "share_of_timed": tot / ms,
+                  "traffic": traffic_tab.get(name)})
+        if roof is None:
+            roof = r
+        if name == "update":
+            roof_update = r
+        if roof is not None and roof_update is not None:
+            break
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -444,6 +501,7 @@ def run_ours(args, rank, world):
                        "n_active_end": rep["n_active"], "drops_moved": rep["n_moved"],
                        "near_contact_steps": rep["near_contact_steps"]},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "roofline_update_pass": roof_update,
             "cpu_baseline": cpu, "fp64_path": fp64,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
     if fp64:

@@ -106,6 +106,7 @@ typedef struct {
     int64_t field_steps;       /* sum over the call's steps of fields advected */
     int64_t faces_network;     /* VOF_MIXED_LEARNED: interfacial faces on the network's normal */
     int64_t faces_myc;         /* ... and on MYC's normal (the fallback) */
+    int64_t faces_myc_judged;  /* faces whose MYC normal and residual were evaluated */
 } vof_step_report;
 
 /*
@@ -393,6 +394,7 @@ typedef struct {
     int64_t cell_fields_per_step;  /* sum over boxes of cells x active fields */
     double clipped_volume[64];     /* per box, accumulated since init */
     int64_t faces_network, faces_myc; /* VOF_MIXED_LEARNED, accumulated */
+    int64_t faces_myc_judged;      /* faces whose MYC residual was evaluated */
     int32_t update_warps, update_blocks_per_sm; /* launch shape in use */
     int32_t tune_candidates;       /* shapes timed by the tuner (0: not tuned) */
     float tune_best_ms;            /* median first-sweep time of the chosen shape */

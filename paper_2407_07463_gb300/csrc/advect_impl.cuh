@@ -307,14 +307,21 @@ void face_fluxes(const BoxSet<T, NB>& S, int d, int sweep, const unsigned long l
                  SweepArgs& a) {
     if constexpr (std::is_same<T, float>::value) {
         if (a.mlp) {
-            face_flux_learned_set<NB>(S, d, sweep, (float)a.band, list, cap, a.offsets, gb, a.tile_seg, a.mlp,
-                                      a.mlp_tol, a.mlp_status, a.mlp_counters, a.stream);
+            if (a.prof) a.prof->begin(P_NET_NORMALS);
+            face_normals_net_set<NB>(S, d, sweep, list, cap, a.offsets, gb, a.tile_seg, a.mlp, a.mlp_status,
+                                     a.stream);
+            if (a.prof) { a.prof->end(); a.prof->begin(P_FACE_FLUX); }
+            face_flux_judged_set<NB>(S, d, sweep, (float)a.band, list, cap, a.offsets, gb, a.tile_seg, a.mlp_tol,
+                                     a.mlp_counters, a.stream);
+            if (a.prof) a.prof->end();
             if (a.launches) *a.launches += 2;
             return;
         }
     }
+    if (a.prof) a.prof->begin(P_FACE_FLUX);
     k_face_flux_bx<T, NB><<<152 * 16, kFaceTile, 0, a.stream>>>(S, d, sweep, (T)a.band, list, cap, a.offsets, gb,
                                                                  a.tile_seg);
+    if (a.prof) a.prof->end();
     if (a.launches) *a.launches += 1;
 }
 
@@ -351,11 +358,12 @@ cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
             // next sweep: within the step, or the first sweep of the next step
             const int dn = sw < 2 ? (rot + sw + 1) % 3 : (int)((step + 1) % 3);
             const int cur = a.list_cur, nxt = 1 - a.list_cur;
-            if (a.prof) a.prof->begin(P_FACE_FLUX);
+            if (a.prof) a.prof->begin(P_SCAN);
             scan_face_counts(counts[cur], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
             if (a.launches) *a.launches += 1;
+            if (a.prof) a.prof->end();
             face_fluxes(S, d, sw, lists[cur], G.cap, G.gb, a);
-            if (a.prof) { a.prof->end(); a.prof->begin(P_UPDATE); }
+            if (a.prof) a.prof->begin(P_UPDATE);
             if (vec) {
                 k_update_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, d, dn, sw, tau, lists[nxt], G.cap,
                                                                       counts[nxt]);

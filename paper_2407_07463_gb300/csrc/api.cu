@@ -48,7 +48,7 @@ enum Slot {
 };
 
 // MISC slot layout (bytes): counters[8] u64 | flags[16] int | clipped[16] double |
-// overflow int | n_out[16] int | vscan[2] u64 | learned-normal status int, face counters[2] u64
+// overflow int | n_out[16] int | vscan[2] u64 | learned-normal status int, face counters[3] u64
 constexpr size_t kMiscCounters = 0;
 constexpr size_t kMiscFlags = 64;
 constexpr size_t kMiscClipped = 128;
@@ -489,6 +489,9 @@ static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
     B.K = ctx->n_active;
     B.item0 = 0;
     B.cpr = (g.nx + CH - 1) / CH;
+    B.divK = fastdiv_make((uint32_t)B.K);
+    B.divcpr = fastdiv_make((uint32_t)B.cpr);
+    B.divny = fastdiv_make((uint32_t)g.ny);
     B.sfac = (T)(dt / ctx->cfg.h);
     B.c = (T*)ctx->c;
     B.b1 = ctx->slot<T>(S_BUF1);
@@ -527,7 +530,7 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     unsigned long long* mlp_counters = (unsigned long long*)(ctx->misc() + kMiscMlpCounters);
     if (report) {
         VOF_CUDA(ctx, cudaMemsetAsync(clipped, 0, kMaxK * sizeof(double), ctx->stream));
-        VOF_CUDA(ctx, cudaMemsetAsync(mlp_counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        VOF_CUDA(ctx, cudaMemsetAsync(mlp_counters, 0, 3 * sizeof(unsigned long long), ctx->stream));
     }
     SweepArgs a;
     a.list = ctx->slot<unsigned long long>(S_LIST);
@@ -578,7 +581,7 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     }
     if (report) {
         double hc[kMaxK];
-        unsigned long long hm[2];
+        unsigned long long hm[3];
         int mst = 0;
         VOF_CUDA(ctx, cudaMemcpyAsync(hc, clipped, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
         VOF_CUDA(ctx, cudaMemcpyAsync(hm, mlp_counters, sizeof(hm), cudaMemcpyDeviceToHost, ctx->stream));
@@ -587,6 +590,7 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
         if (mst) return ctx->sticky = VOF_ERR_TIMEOUT;
         report->faces_network = (int64_t)hm[0];
         report->faces_myc = (int64_t)hm[1];
+        report->faces_myc_judged = (int64_t)hm[2];
         double tot = 0.0;
         for (int f = 0; f < ctx->cfg.k_capacity; ++f) tot += hc[f];
         report->steps_done = ctx->step;
@@ -930,7 +934,7 @@ const char* vof_last_cuda_error(void) { return vof::last_cuda_error_name(); }
 const char* vof_profile_class_name(int32_t cls) {
     static const char* names[P_COUNT] = {"list_faces", "face_flux", "update", "pack_bits", "near_contact",
                                          "label",      "pairs",     "touch",  "move",      "stats",
-                                         "misc",       "net_normals"};
+                                         "misc",       "net_normals", "scan"};
     if (cls < 0 || cls >= P_COUNT) return nullptr;
     return names[cls];
 }

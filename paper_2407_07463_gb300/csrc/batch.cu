@@ -79,7 +79,7 @@ BatchLayout batch_layout(const vof_batch_config* cfg, const vof_box_desc* boxes,
     L.list = o, o = al256(o + 2 * (size_t)L.list_entries * 8);
     L.counts = o, o = al256(o + (3 * (size_t)kSweepBlocks + 1) * 4);
     L.tile_seg = o, o = al256(o + ((size_t)L.tile_cap + 1) * 4);
-    L.misc = o, o = al256(o + 64);  // [0] tensor-core status, [8..24) face counters
+    L.misc = o, o = al256(o + 64);  // [0] tensor-core status, [8..32) face counters
     L.vscan = o, o = al256(o + 16);
     L.total = o;
     return L;
@@ -122,6 +122,9 @@ BoxSet<T, kMaxBoxes> batch_set(vof_batch* B) {
         X.K = d.k_active;
         X.item0 = item;
         X.cpr = (d.nx + CH - 1) / CH;
+        X.divK = fastdiv_make((uint32_t)X.K);
+        X.divcpr = fastdiv_make((uint32_t)X.cpr);
+        X.divny = fastdiv_make((uint32_t)d.ny);
         X.sfac = (T)(d.dt / B->cfg.h);
         X.c = (T*)d.c_dev;
         X.b1 = (T*)(B->ws + B->L.b1[b]);
@@ -387,7 +390,7 @@ vof_status vof_batch_tune(vof_batch* B) {
     B->tune_ms_best = best;
     B->tune_candidates = n;
     // the timed sweeps counted faces: start the counters afresh
-    if (cudaMemsetAsync(B->ws + B->L.misc + 8, 0, 16, B->stream) != cudaSuccess) return fail(B, VOF_ERR_CUDA);
+    if (cudaMemsetAsync(B->ws + B->L.misc + 8, 0, 24, B->stream) != cudaSuccess) return fail(B, VOF_ERR_CUDA);
     for (auto& r : B->graphs)
         for (auto& g : r)
             if (g) cudaGraphExecDestroy(g), g = nullptr;
@@ -434,11 +437,11 @@ vof_status vof_batch_report(vof_batch* B, vof_batch_report_t* r) {
     if (!B || !r) return VOF_ERR_ARG;
     const int n = (int)B->boxes.size();
     std::vector<double> cl((size_t)n * 16);
-    unsigned long long cnt[2];
+    unsigned long long cnt[3];
     int st = 0;
     if (cudaMemcpyAsync(cl.data(), B->ws + B->L.clipped, cl.size() * 8, cudaMemcpyDeviceToHost, B->stream) !=
             cudaSuccess ||
-        cudaMemcpyAsync(cnt, B->ws + B->L.misc + 8, 16, cudaMemcpyDeviceToHost, B->stream) != cudaSuccess ||
+        cudaMemcpyAsync(cnt, B->ws + B->L.misc + 8, 24, cudaMemcpyDeviceToHost, B->stream) != cudaSuccess ||
         cudaMemcpyAsync(&st, B->ws + B->L.misc, 4, cudaMemcpyDeviceToHost, B->stream) != cudaSuccess ||
         cudaStreamSynchronize(B->stream) != cudaSuccess)
         return fail(B, VOF_ERR_CUDA);
@@ -456,6 +459,7 @@ vof_status vof_batch_report(vof_batch* B, vof_batch_report_t* r) {
     r->cell_fields_per_step = fs;
     r->faces_network = (int64_t)cnt[0];
     r->faces_myc = (int64_t)cnt[1];
+    r->faces_myc_judged = (int64_t)cnt[2];
     r->update_warps = B->update_warps;
     r->update_blocks_per_sm = B->update_blocks_per_sm;
     r->tune_candidates = B->tune_candidates;

@@ -24,12 +24,37 @@
 
 namespace vof {
 
+// Division by a fixed positive divisor d through a multiply-high (the
+// round-up method of Granlund & Montgomery 1994), exact for n < 2^31: with
+// 2^(l-1) < d < 2^l, mul = ceil(2^(31+l) / d) < 2^32 and
+// q = umulhi(n, mul) >> (l - 1); a power of two is a shift.
+struct FastDiv {
+    uint32_t mul, sh;  // mul == 0: q = n >> sh
+};
+__host__ inline FastDiv fastdiv_make(uint32_t d) {
+    FastDiv f;
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    if ((1ull << l) == d) {
+        f.mul = 0;
+        f.sh = l;
+    } else {
+        f.mul = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+        f.sh = l - 1;
+    }
+    return f;
+}
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv& f) {
+    return f.mul == 0 ? (n >> f.sh) : (__umulhi(n, f.mul) >> f.sh);
+}
+
 template <typename T>
 struct BoxDev {
     Dims g;
     int K;      // fields advected
     int item0;  // first work item of the box
     int cpr;    // row chunks per row, ceil(nx / (32 VW))
+    FastDiv divK, divcpr, divny;  // by K, cpr and ny
     T sfac;     // dt / h
     T* c;       // [K][N] state (updated in place over a step)
     T* b1;      // [K][N] state after the first sweep
@@ -88,9 +113,9 @@ __device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, i
     constexpr int VW = VecOf<T>::W;
     const Dims& g = B.g;
     ItemCells r;
-    const int chunk = local / B.K;
+    const int chunk = (int)fastdiv((uint32_t)local, B.divK);
     r.f = local - chunk * B.K;
-    r.row = chunk / B.cpr;
+    r.row = (int)fastdiv((uint32_t)chunk, B.divcpr);
     const int seg = chunk - r.row * B.cpr;
     const int i0 = seg * 32 * VW + lane * VW;
     r.valid = i0 < g.nx;
@@ -98,8 +123,8 @@ __device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, i
     // stays in the grid) and write nothing
     r.i0 = r.valid ? i0 : 0;
     r.x0 = r.row * g.nx + r.i0;
-    r.j = r.row % g.ny;
-    r.k = r.row / g.ny;
+    r.k = (int)fastdiv((uint32_t)r.row, B.divny);
+    r.j = r.row - r.k * g.ny;
     const int plane = g.nx * g.ny;
     r.lo_y = r.j == 0 ? (g.ny - 1) * g.nx : -g.nx;
     r.hi_y = r.j == g.ny - 1 ? -(g.ny - 1) * g.nx : g.nx;

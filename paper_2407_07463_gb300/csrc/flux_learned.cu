@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
     __shared__ int s_nf;
     const int t = threadIdx.x;
     const int n = off[nseg];
-    unsigned n_net = 0, n_myc = 0;
+    unsigned n_net = 0, n_myc = 0, n_queued = 0;
     for (int base = blockIdx.x * 128; base < n; base += gridDim.x * 128) {
         const int e = base + t;
         const bool valid = e < n;
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
             }
         }
         __syncthreads();
+        if (t == 0) n_queued += s_nf;
         // MYC's normal and residual for the queued faces, on the first threads
         if (t < s_nf) {
             const int u = s_list[t];
@@ -160,12 +161,13 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
         if (n_net) atomicAdd(&counters[0], (unsigned long long)n_net);
         if (n_myc) atomicAdd(&counters[1], (unsigned long long)n_myc);
     }
+    if (t == 0 && counters && n_queued) atomicAdd(&counters[2], (unsigned long long)n_queued);
 }
 
 template <int NB>
-void face_flux_learned_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
-                           long long cap, const int* off, int nseg, const int* tile_seg, const MlpBlob* w,
-                           float tol, int* status, unsigned long long* counters, cudaStream_t st) {
+void face_normals_net_set(const BoxSet<float, NB>& S, int d, int sweep, const unsigned long long* list, long long cap,
+                          const int* off, int nseg, const int* tile_seg, const MlpBlob* w, int* status,
+                          cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_face_normals_net<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -174,14 +176,24 @@ void face_flux_learned_set(const BoxSet<float, NB>& S, int d, int sweep, float b
     }
     k_face_normals_net<NB><<<152 * 4, 128, sizeof(MlpSmem), st>>>(S, d, sweep, list, cap, off, nseg, tile_seg, w,
                                                                   status);
+}
+
+template <int NB>
+void face_flux_judged_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
+                          long long cap, const int* off, int nseg, const int* tile_seg, float tol,
+                          unsigned long long* counters, cudaStream_t st) {
     k_face_flux_judged<NB><<<152 * 16, 128, 0, st>>>(S, d, sweep, band, list, cap, off, nseg, tile_seg, tol, counters);
 }
 
-template void face_flux_learned_set<1>(const BoxSet<float, 1>&, int, int, float, const unsigned long long*, long long,
-                                       const int*, int, const int*, const MlpBlob*, float, int*, unsigned long long*,
-                                       cudaStream_t);
-template void face_flux_learned_set<kMaxBoxes>(const BoxSet<float, kMaxBoxes>&, int, int, float,
-                                               const unsigned long long*, long long, const int*, int, const int*,
-                                               const MlpBlob*, float, int*, unsigned long long*, cudaStream_t);
+#define VOF_LEARNED_SET(NB)                                                                                       \
+    template void face_normals_net_set<NB>(const BoxSet<float, NB>&, int, int, const unsigned long long*,         \
+                                           long long, const int*, int, const int*, const MlpBlob*, int*,          \
+                                           cudaStream_t);                                                         \
+    template void face_flux_judged_set<NB>(const BoxSet<float, NB>&, int, int, float, const unsigned long long*,  \
+                                           long long, const int*, int, const int*, float, unsigned long long*,    \
+                                           cudaStream_t);
+VOF_LEARNED_SET(1)
+VOF_LEARNED_SET(kMaxBoxes)
+#undef VOF_LEARNED_SET
 
 }  // namespace vof

@@ -24,6 +24,7 @@ enum ProfClass {
     P_STATS,
     P_MISC,
     P_NET_NORMALS,
+    P_SCAN,
     P_COUNT
 };
 
@@ -66,13 +67,17 @@ struct BoxSet;
 constexpr int kMaxBoxes = 64;
 // Largest grid of the list-producing passes.
 constexpr int kListBlocks = 2048;
-// Network normals, then judged fluxes, of the listed faces of one sweep of
-// a box set (FP32 path with the learned normal); counters[0/1] += faces on
-// the network's / MYC's normal.
+// Learned normal of a box set (FP32 path): network normals of the listed
+// faces of one sweep (tensor cores), then their judged fluxes;
+// counters[0/1] += faces on the network's / MYC's normal.
 template <int NB>
-void face_flux_learned_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
-                           long long cap, const int* off, int nseg, const int* tile_seg, const MlpBlob* w,
-                           float tol, int* status, unsigned long long* counters, cudaStream_t st);
+void face_normals_net_set(const BoxSet<float, NB>& S, int d, int sweep, const unsigned long long* list, long long cap,
+                          const int* off, int nseg, const int* tile_seg, const MlpBlob* w, int* status,
+                          cudaStream_t st);
+template <int NB>
+void face_flux_judged_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
+                          long long cap, const int* off, int nseg, const int* tile_seg, float tol,
+                          unsigned long long* counters, cudaStream_t st);
 // nsteps steps of every box of a set (one box: a context; up to kMaxBoxes:
 // a batch).
 cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps);

@@ -46,7 +46,7 @@ class vof_step_report(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("clipped_volume", C.c_double),
                 ("n_active", C.c_int32), ("n_moved", C.c_int32),
                 ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64),
-                ("faces_network", C.c_int64), ("faces_myc", C.c_int64)]
+                ("faces_network", C.c_int64), ("faces_myc", C.c_int64), ("faces_myc_judged", C.c_int64)]
 
 
 class vof_box_desc(C.Structure):
@@ -62,6 +62,7 @@ class vof_batch_config(C.Structure):
 class vof_batch_report_t(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("n_boxes", C.c_int32), ("cell_fields_per_step", C.c_int64),
                 ("clipped_volume", C.c_double * 64), ("faces_network", C.c_int64), ("faces_myc", C.c_int64),
+                ("faces_myc_judged", C.c_int64),
                 ("update_warps", C.c_int32), ("update_blocks_per_sm", C.c_int32),
                 ("tune_candidates", C.c_int32), ("tune_best_ms", C.c_float), ("graph_launches", C.c_int64),
                 ("direct_steps", C.c_int64)]
@@ -378,7 +379,8 @@ class Context:
         return {"status": st, "steps_done": rep.steps_done, "clipped_volume": rep.clipped_volume,
                 "n_active": rep.n_active, "n_moved": rep.n_moved,
                 "near_contact_steps": rep.near_contact_steps, "field_steps": rep.field_steps,
-                "faces_network": rep.faces_network, "faces_myc": rep.faces_myc}
+                "faces_network": rep.faces_network, "faces_myc": rep.faces_myc,
+                "faces_myc_judged": rep.faces_myc_judged}
 
     step = vof_step
 
