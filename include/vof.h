@@ -310,6 +310,12 @@ typedef struct {
     double test_mean_deg_combined; /* network with MYC fallback (residual judge, tol 1e-3) */
     double test_p95_deg_combined;
     double test_network_share;  /* share of held-out stencils that keep the network's normal */
+    /* held-out means by class: 0 planes, spheres of radius 1: [2,4), 2: [4,8),
+     * 3: [8,16), 4: [16, r_max] cells */
+    int64_t bin_count[5];
+    double bin_mean_deg_mlp[5];
+    double bin_mean_deg_myc[5];
+    double bin_mean_deg_combined[5];
 } vof_train_report;
 
 vof_status vof_mlp_train_params_default(vof_train_params *tp);

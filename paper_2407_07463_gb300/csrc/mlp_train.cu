@@ -89,8 +89,9 @@ __device__ double sphere_fraction(const double C[3], double R, int i, int j, int
     return fmin(1.0, acc / (NS * NS));
 }
 
-__global__ void k_mlp_gen(float* __restrict__ st, float* __restrict__ tgt, long long n, uint64_t seed,
-                          double plane_frac, double r_min, double r_max) {
+// rad (may be null) receives each sample's sphere radius, 0 for a plane.
+__global__ void k_mlp_gen(float* __restrict__ st, float* __restrict__ tgt, float* __restrict__ rad, long long n,
+                          uint64_t seed, double plane_frac, double r_min, double r_max) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
         double t[3];
@@ -109,6 +110,7 @@ __global__ void k_mlp_gen(float* __restrict__ st, float* __restrict__ tgt, long 
             t[0] = nv[0];
             t[1] = nv[1];
             t[2] = nv[2];
+            if (rad) rad[s] = 0.f;
         } else {
             double R = exp(log(r_min) + urand(seed, s, 4) * (log(r_max) - log(r_min)));
             double dir[3];
@@ -127,6 +129,7 @@ __global__ void k_mlp_gen(float* __restrict__ st, float* __restrict__ tgt, long 
             t[0] = sg * dir[0];
             t[1] = sg * dir[1];
             t[2] = sg * dir[2];
+            if (rad) rad[s] = (float)R;
         }
         tgt[s * 3 + 0] = (float)t[0];
         tgt[s * 3 + 1] = (float)t[1];
@@ -418,10 +421,17 @@ __global__ void k_params_to_blob(const float* __restrict__ p, MlpBlob* __restric
 // ---------------------------------------------------------------------------
 // held-out evaluation: angle (degrees) between target and MLP / MYC normals
 
+// Class of a held-out sample: 0 plane, 1..4 sphere radius in [2,4), [4,8),
+// [8,16), [16, inf).
+__device__ __forceinline__ int radius_bin(float r) {
+    return r <= 0.f ? 0 : (r < 4.f ? 1 : (r < 8.f ? 2 : (r < 16.f ? 3 : 4)));
+}
+
 __global__ void k_mlp_eval_angles(const float* __restrict__ st, const float* __restrict__ tgt,
-                                  const float* __restrict__ n_mlp, long long n, float tol,
-                                  unsigned* __restrict__ hist_mlp, unsigned* __restrict__ hist_myc,
-                                  unsigned* __restrict__ hist_cmb, double* __restrict__ sums) {
+                                  const float* __restrict__ rad, const float* __restrict__ n_mlp, long long n,
+                                  float tol, unsigned* __restrict__ hist_mlp, unsigned* __restrict__ hist_myc,
+                                  unsigned* __restrict__ hist_cmb, double* __restrict__ sums,
+                                  double* __restrict__ bins) {
     double s_mlp = 0.0, s_myc = 0.0, s_cmb = 0.0, s_used = 0.0;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         float sv[27];
@@ -438,8 +448,15 @@ __global__ void k_mlp_eval_angles(const float* __restrict__ st, const float* __r
         // the estimator as the method uses it: the network unless its plane
         // explains the neighbours worse than MYC's and than the tolerance
         const float nn[3] = {n_mlp[r * 3], n_mlp[r * 3 + 1], n_mlp[r * 3 + 2]};
-        const bool use = normal_residual(sv, nn) <= fmaxf(tol, normal_residual(sv, m));
+        float mj[3];
+        const bool use = judged_normal(sv, nn, tol, mj);
         const float a3 = use ? a2 : a1;
+        // per class: count, mean angle of the network, of MYC, of the judged estimator
+        double* bq = bins + 4 * radius_bin(rad[r]);
+        atomicAdd(bq, 1.0);
+        atomicAdd(bq + 1, (double)a2);
+        atomicAdd(bq + 2, (double)a1);
+        atomicAdd(bq + 3, (double)a3);
         s_myc += a1;
         s_mlp += a2;
         s_cmb += a3;
@@ -481,7 +498,7 @@ int* train_status_ptr() {
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct TrainLayout {
-    size_t st, tgt, test_st, test_tgt, test_n, p, g, m, v, loss, hist, sums, total;
+    size_t st, tgt, test_st, test_tgt, test_n, p, g, m, v, loss, hist, sums, bins, test_rad, total;
 };
 
 TrainLayout train_layout(const vof_train_params* tp) {
@@ -499,6 +516,8 @@ TrainLayout train_layout(const vof_train_params* tp) {
     L.loss = o; o = align_up(o + 8);
     L.hist = o; o = align_up(o + 3 * 18000 * 4);
     L.sums = o; o = align_up(o + 4 * 8);
+    L.bins = o; o = align_up(o + 5 * 4 * 8);
+    L.test_rad = o; o = align_up(o + (size_t)tp->n_test * 4);
     L.total = o;
     return L;
 }
@@ -567,10 +586,11 @@ extern "C" vof_status vof_mlp_train(const vof_train_params* tp, void* weights_de
     } while (0)
     TRY(cudaMemsetAsync(status, 0, 4, st));
     // data
-    k_mlp_gen<<<152 * 16, 128, 0, st>>>(dst, dtg, tp->n_train, tp->seed, tp->plane_fraction, tp->r_min, tp->r_max);
+    k_mlp_gen<<<152 * 16, 128, 0, st>>>(dst, dtg, nullptr, tp->n_train, tp->seed, tp->plane_fraction, tp->r_min,
+                                        tp->r_max);
     if (tp->n_test > 0)
-        k_mlp_gen<<<152 * 16, 128, 0, st>>>(tst, ttg, tp->n_test, host_mix64(tp->seed + 1), tp->plane_fraction,
-                                            tp->r_min, tp->r_max);
+        k_mlp_gen<<<152 * 16, 128, 0, st>>>(tst, ttg, (float*)(ws + L.test_rad), tp->n_test, host_mix64(tp->seed + 1),
+                                            tp->plane_fraction, tp->r_min, tp->r_max);
     TRY(cudaGetLastError());
     // initial weights: He-normal hidden layers (Box-Muller on a counter RNG), zero biases
     std::vector<float> hp(kNParam, 0.f);
@@ -619,16 +639,20 @@ extern "C" vof_status vof_mlp_train(const vof_train_params* tp, void* weights_de
     float hloss = 0.f;
     TRY(cudaMemcpyAsync(&hloss, loss, 4, cudaMemcpyDeviceToHost, st));
     double hs[4] = {0.0, 0.0, 0.0, 0.0};
+    double hb[5][4] = {};
     std::vector<unsigned> hh(54000, 0u);
     if (tp->n_test > 0) {
         int* fstat = status;
         TRY(mlp_forward(blob, tst, tnm, tp->n_test, fstat, st));
         TRY(cudaMemsetAsync(hist, 0, 3 * 18000 * 4, st));
         TRY(cudaMemsetAsync(sums, 0, 32, st));
-        k_mlp_eval_angles<<<152 * 8, 128, 0, st>>>(tst, ttg, tnm, tp->n_test, 1e-3f, hist, hist + 18000,
-                                                   hist + 36000, sums);
+        TRY(cudaMemsetAsync(ws + L.bins, 0, 5 * 4 * 8, st));
+        k_mlp_eval_angles<<<152 * 8, 128, 0, st>>>(tst, ttg, (const float*)(ws + L.test_rad), tnm, tp->n_test,
+                                                   1e-3f, hist, hist + 18000, hist + 36000, sums,
+                                                   (double*)(ws + L.bins));
         TRY(cudaGetLastError());
         TRY(cudaMemcpyAsync(hs, sums, 32, cudaMemcpyDeviceToHost, st));
+        TRY(cudaMemcpyAsync(hb, ws + L.bins, sizeof(hb), cudaMemcpyDeviceToHost, st));
         TRY(cudaMemcpyAsync(hh.data(), hist, 54000 * 4, cudaMemcpyDeviceToHost, st));
     }
     int hstat = 0;
@@ -654,6 +678,13 @@ extern "C" vof_status vof_mlp_train(const vof_train_params* tp, void* weights_de
         report->test_mean_deg_combined = tp->n_test ? hs[2] / tp->n_test : 0.0;
         report->test_p95_deg_combined = tp->n_test ? p95(hh.data() + 36000) : 0.0;
         report->test_network_share = tp->n_test ? hs[3] / tp->n_test : 0.0;
+        for (int b = 0; b < 5; ++b) {
+            const double cnt = hb[b][0];
+            report->bin_count[b] = (int64_t)cnt;
+            report->bin_mean_deg_mlp[b] = cnt > 0 ? hb[b][1] / cnt : 0.0;
+            report->bin_mean_deg_myc[b] = cnt > 0 ? hb[b][2] / cnt : 0.0;
+            report->bin_mean_deg_combined[b] = cnt > 0 ? hb[b][3] / cnt : 0.0;
+        }
     }
     return VOF_OK;
 }

@@ -79,7 +79,9 @@ class vof_train_report(C.Structure):
                 ("test_mean_deg_mlp", C.c_double), ("test_mean_deg_myc", C.c_double),
                 ("test_p95_deg_mlp", C.c_double), ("test_p95_deg_myc", C.c_double),
                 ("test_mean_deg_combined", C.c_double), ("test_p95_deg_combined", C.c_double),
-                ("test_network_share", C.c_double)]
+                ("test_network_share", C.c_double), ("bin_count", C.c_int64 * 5),
+                ("bin_mean_deg_mlp", C.c_double * 5), ("bin_mean_deg_myc", C.c_double * 5),
+                ("bin_mean_deg_combined", C.c_double * 5)]
 
 
 class vof_stats_out(C.Structure):
@@ -306,7 +308,11 @@ def vof_mlp_train(tp, device="cuda", stream=None):
     _check(lib().vof_mlp_train(C.byref(tp), _ptr(w), _ptr(ws), nbytes, _stream(stream), C.byref(rep)),
            "vof_mlp_train")
     del ws
-    return w, {k: getattr(rep, k) for k, _ in vof_train_report._fields_}
+    out = {}
+    for k, _ in vof_train_report._fields_:
+        v = getattr(rep, k)
+        out[k] = list(v) if k.startswith("bin_") else v
+    return w, out
 
 
 def vof_learned_normals(weights, stencils, fallback_tol=1e-3, stream=None):

@@ -106,8 +106,8 @@ def test_training_gains_over_myc(vof):
     """Train on 4M generated stencils (planes and spheres); on held-out
     stencils the network's 95th-percentile angular error is below MYC's, and
     the estimator as the step uses it (network, MYC fallback when the
-    network's plane explains the six face neighbours worse than MYC's and
-    worse than 1e-3) beats MYC on both the mean and the 95th percentile."""
+    network's plane explains the 3x3x3 block worse than MYC's and worse than
+    1e-3) beats MYC on both the mean and the 95th percentile."""
     tp = vof.train_params(n_train=4_000_000, n_test=200_000, epochs=4, batch=16384, seed=7)
     w, rep = vof.vof_mlp_train(tp, DEV)
     print(rep)
@@ -115,6 +115,14 @@ def test_training_gains_over_myc(vof):
     assert rep["test_p95_deg_mlp"] < rep["test_p95_deg_myc"]
     assert rep["test_mean_deg_combined"] < rep["test_mean_deg_myc"]
     assert rep["test_p95_deg_combined"] < rep["test_p95_deg_myc"]
+    # by class: the network's gain is on curved interfaces (sphere radius
+    # 2-16 cells; 2.6 -> 1.0 degrees at radius 2-4).  On planes and on
+    # radius 16-32 MYC stays ahead (its centred columns are exact for
+    # unsaturated planes), and the judged estimator keeps MYC there.
+    assert all(c > 1000 for c in rep["bin_count"])
+    for b in (1, 2, 3):
+        assert rep["bin_mean_deg_mlp"][b] < rep["bin_mean_deg_myc"][b], b
+    assert rep["bin_mean_deg_combined"][0] <= rep["bin_mean_deg_myc"][0] + 0.05
 
 
 @pytest.mark.parametrize("radius", [4.0, 8.0])
