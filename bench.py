@@ -385,15 +385,9 @@ def run_ours(args, rank, world):
     prof = ctx.vof_profile_read()
     ctx.vof_profile_enable(False)
     updates = N * rep["field_steps"]
-    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device=dev)
-    if dist:
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(tmax[0]), float(tsum[0])
-    else:
-        ms_max, updates_all = ms, float(updates)
+    from paper_2407_07463_gb300 import scaling
+
+    ms_max, updates_all = scaling.aggregate(ms, updates, device=dev)
     value = updates_all / (ms_max * 1e-3)
 
     # e2e through the public API with host buffers: per step, pinned H2D of
