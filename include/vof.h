@@ -429,6 +429,12 @@ vof_status vof_batch_step(vof_batch *batch, int32_t nsteps);
 vof_status vof_batch_report(vof_batch *batch, vof_batch_report_t *report);
 void vof_batch_destroy(vof_batch *batch);
 
+/* Exercises the bounded device wait of the tensor-core kernels on an
+ * mbarrier that nothing arrives at: the wait gives up after poll_limit
+ * polls (1..1e8) and the call returns VOF_ERR_TIMEOUT with the device
+ * still usable.  For tests of the failure path; no fault is raised. */
+vof_status vof_wait_selftest(int64_t poll_limit, void *stream);
+
 const char *vof_status_string(vof_status s);
 /* Name of the last CUDA error a call of this thread met and reported as
  * VOF_ERR_CUDA ("no error" if none). */

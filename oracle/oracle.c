@@ -17,11 +17,20 @@
  *     (breadth-first flood fill), near-contact pairs with distinct tags,
  *     recolouring into free fields.
  *   - Section 3: drop centroids from tags and nearest-particle statistics.
+ *   - The learned normal (no counterpart in the paper): canonical frame of a
+ *     stencil, the 27-64-64-3 network in FP64 (optionally with the BF16
+ *     rounding of weights and layer inputs the tensor cores see), FP64
+ *     backpropagation, the 27-cell residual that judges a normal, the MYC
+ *     fallback, and the split step with that normal.
  *
  * Parity pins: every function is pinned by tests against closed forms,
  * brute force and the paper's worked example, except the MYC selection rule
- * itself (pinned only through the cases where all candidates coincide) --
- * "parity unpinned" for that rule.
+ * itself (pinned only through the cases where all candidates coincide and
+ * the exactness of centred columns on unsaturated planes) -- "parity
+ * unpinned" for that rule -- and the fallback rule of the learned normal,
+ * which the paper does not have (its parts are pinned: the network by a
+ * weight set that reproduces Youngs, the residual by hand-computed axis
+ * planes and exact planes, backpropagation by finite differences).
  *
  * Build with -ffp-contract=off so x86-64 and aarch64 round identically.
  */

@@ -232,6 +232,29 @@ extern "C" vof_status vof_learned_normals(const void* weights_dev, const float* 
     return read_status(st);
 }
 
+namespace vof {
+// An mbarrier that nothing arrives at, waited on with the bounded wait the
+// tensor-core kernels use: the wait gives up after `limit` polls and the
+// kernel reports it, the context stays usable.
+__global__ void k_wait_selftest(long long limit, int* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = tc::mbar_wait(&bar, 0u, limit);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicExch(status, 1);
+}
+}  // namespace vof
+
+extern "C" vof_status vof_wait_selftest(int64_t poll_limit, void* stream) {
+    if (poll_limit < 1 || poll_limit > 100000000LL) return VOF_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* sp = status_ptr();
+    if (!sp || cudaMemsetAsync(sp, 0, sizeof(int), st) != cudaSuccess) return VOF_ERR_CUDA;
+    vof::k_wait_selftest<<<1, 32, 0, st>>>(poll_limit, sp);
+    if (cudaGetLastError() != cudaSuccess) return VOF_ERR_CUDA;
+    return read_status(st);
+}
+
 extern "C" vof_status vof_tc_gemm_check(const float* a_dev, const float* b_dev, float* d_dev, int32_t k,
                                         int32_t n, int32_t variant, void* stream) {
     if (!a_dev || !b_dev || !d_dev || (k != 16 && k != 32 && k != 64) || (n != 16 && n != 32 && n != 64))

@@ -103,7 +103,7 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals",
            "vof_batch_config_default", "vof_batch_workspace_size", "vof_batch_init", "vof_batch_set_mlp",
            "vof_batch_tune", "vof_batch_step", "vof_batch_report", "vof_batch_destroy",
-           "vof_last_cuda_error"]
+           "vof_last_cuda_error", "vof_wait_selftest"]
 
 
 def lib():
@@ -162,6 +162,7 @@ def lib():
         "vof_batch_report": (C.c_int, [vp, C.POINTER(vof_batch_report_t)]),
         "vof_batch_destroy": (None, [vp]),
         "vof_last_cuda_error": (C.c_char_p, []),
+        "vof_wait_selftest": (C.c_int, [i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -325,6 +326,12 @@ def vof_learned_normals(weights, stencils, fallback_tol=1e-3, stream=None):
     _check(lib().vof_learned_normals(_ptr(weights), _ptr(stencils), n, float(fallback_tol), _ptr(m),
                                      _ptr(which), _stream(stream)), "vof_learned_normals")
     return m, which
+
+
+def vof_wait_selftest(poll_limit=100000, stream=None):
+    """Runs the bounded-wait self-test; returns its status (VOF_ERR_TIMEOUT
+    expected)."""
+    return lib().vof_wait_selftest(int(poll_limit), _stream(stream))
 
 
 def vof_tc_gemm_check(a, b, variant=0, stream=None):

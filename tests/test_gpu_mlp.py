@@ -37,6 +37,16 @@ def test_tensor_core_operand_layout(vof, k, n):
     assert np.abs(d - want).max() <= 1e-5 * np.abs(want).max()
 
 
+def test_bounded_wait_gives_up_and_device_stays_usable(vof):
+    """A wait on an mbarrier that nothing arrives at returns VOF_ERR_TIMEOUT
+    (no fault); the next tensor-core call still works."""
+    assert vof.vof_wait_selftest(100000) == vof.VOF_ERR_TIMEOUT
+    A = torch.ones((128, 16), device=DEV)
+    B = torch.ones((16, 16), device=DEV)
+    d = vof.vof_tc_gemm_check(A, B).cpu().numpy()
+    assert np.all(d == 16.0)
+
+
 def random_params(rng, scale=0.25):
     p = rng.normal(size=O.MLP_NPARAM) * scale
     p[0:2048].reshape(64, 32)[:, 27:] = 0.0          # W1 padding columns
