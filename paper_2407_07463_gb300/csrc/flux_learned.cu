@@ -53,8 +53,13 @@ __global__ void __launch_bounds__(128, 4) k_face_normals_net(const __grid_consta
         }
         CanonFrame fr;
         canon_frame(st, fr);
+        // the stencil through this thread's scratch column, so that the
+        // frame's offsets index shared memory rather than registers
+        float* col = stencil_scratch(s) + t;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) col[q * 128] = st[q];
         float x[27];
-        canon_input(st, fr, x);
+        canon_input_col(col, 128, fr, x);
         store_input_row(s, t, x);
         float oc[3];
         if (!mlp_tile_forward(s, taddr, phase, oc)) break;

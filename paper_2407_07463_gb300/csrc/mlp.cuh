@@ -86,6 +86,41 @@ __device__ __forceinline__ void store_pair(unsigned char* tile, int r, int k, in
     *reinterpret_cast<__nv_bfloat16*>(tile + tc::kmajor_offset(r, k + half, kext)) = lo;
 }
 
+// Eight consecutive layer inputs v[0..7] of row r (columns k0..k0+7, k0 a
+// multiple of 8) as pairs: one 16-byte store of the high parts at column k0
+// and one of the low parts at column k0 + half (a core-matrix row holds 8
+// consecutive K elements).
+__device__ __forceinline__ void store_pairs8(unsigned char* tile, int r, int k0, int half, int kext, const float v[8]) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(v[2 * q], h0, l0);
+        split_bf16(v[2 * q + 1], h1, l1);
+        hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(r, k0, kext)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(r, k0 + half, kext)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// x[q] = canonical stencil value - 1/2 from a stencil held as a column of a
+// shared-memory tile (value of cell q at col[q * stride]): the frame's
+// reflections and permutation become one offset per canonical axis.
+__device__ __forceinline__ void canon_input_col(const float* col, int stride, const CanonFrame& fr, float x[27]) {
+    const int step[3] = {1, 3, 9};
+    int s[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q] = fr.sign[fr.perm[q]] * step[fr.perm[q]];
+#pragma unroll
+    for (int kc = -1; kc <= 1; ++kc)
+#pragma unroll
+        for (int jc = -1; jc <= 1; ++jc)
+#pragma unroll
+            for (int ic = -1; ic <= 1; ++ic)
+                x[(kc + 1) * 9 + (jc + 1) * 3 + (ic + 1)] = col[(13 + ic * s[0] + jc * s[1] + kc * s[2]) * stride] - 0.5f;
+}
+
 // Weight matrix w[rows][cols] (global, BF16) into a K-major tile holding it
 // twice along K: columns c and cols + c.
 __device__ __forceinline__ void load_weight_pair(unsigned char* tile, const __nv_bfloat16* __restrict__ w, int rows,

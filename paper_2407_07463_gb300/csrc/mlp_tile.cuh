@@ -47,7 +47,20 @@ __device__ __forceinline__ void load_weights(MlpSmem& s, const MlpBlob* __restri
 
 // Row t of the layer-1 input tile: BF16 high parts, then low parts.
 __device__ __forceinline__ void store_input_row(MlpSmem& s, int t, const float x[27]) {
-    for (int q = 0; q < kIn; ++q) store_pair(s.H, t, q, kIn, kInHL, q < 27 ? x[q] : 0.f);
+#pragma unroll
+    for (int k0 = 0; k0 < kIn; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = k0 + q < 27 ? x[k0 + q] : 0.f;
+        store_pairs8(s.H, t, k0, kIn, kInHL, v);
+    }
+}
+
+// Float scratch [27][128] in the upper half of H (bytes 16 K .. 30 K), free
+// while the layer-1 input (the lower 16 K) is being written: a stencil per
+// thread column, read back with the frame's offsets.
+__device__ __forceinline__ float* stencil_scratch(MlpSmem& s) {
+    return reinterpret_cast<float*>(s.H + 128 * kInHL * 2);
 }
 
 // Tensor-memory columns of the three layer outputs.
@@ -98,7 +111,10 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     for (int c0 = 0; c0 < kHid; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + lane_off + kColD1 + c0, v);
-        for (int q = 0; q < 16; ++q) store_pair(s.H, t, c0 + q, kHid, kHidHL, fmaxf(v[q] + s.b1[c0 + q], 0.f));
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + s.b1[c0 + q], 0.f);
+        store_pairs8(s.H, t, c0, kHid, kHidHL, v);
+        store_pairs8(s.H, t, c0 + 8, kHid, kHidHL, v + 8);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -113,7 +129,8 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
         for (int q = 0; q < 16; ++q) h2[c0 + q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
     }
     // layer 2 has finished reading H: reuse it for layer 3's input
-    for (int q = 0; q < kHid; ++q) store_pair(s.H, t, q, kHid, kHidHL, h2[q]);
+#pragma unroll
+    for (int k0 = 0; k0 < kHid; k0 += 8) store_pairs8(s.H, t, k0, kHid, kHidHL, h2 + k0);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
