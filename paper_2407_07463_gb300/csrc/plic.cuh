@@ -163,6 +163,25 @@ __device__ __forceinline__ float vol_fast(float a, float b, float c, float S, fl
     return alpha <= 0.f ? 0.f : (alpha >= S ? 1.f : r);
 }
 
+// d vol_fast / d alpha (the cut area of the plane in the cube), by the same
+// nested divided differences one order lower: with E(x) = x_+^2,
+//   dV/dalpha = [G(alpha) - G(alpha - c)] / (2c),  G(x) = [F(x) - F(x - b)] / b,
+//   F(x) = [E(x) - E(x - a)] / a = 2x - a (x >= a), x^2 / a (0 < x < a), 0.
+__device__ __forceinline__ float vdf1(float x, float a) {
+    return x >= a ? 2.f * x - a : (x > 0.f ? x * x / a : 0.f);
+}
+__device__ __forceinline__ float vdf2(float x, float a, float b) {
+    const float lin = 2.f;
+    const float dir = (vdf1(x, a) - vdf1(x - b, a)) / b;
+    const float der = x >= a ? 2.f : (x > 0.f ? 2.f * x / a : 0.f);
+    return b <= 1e-30f ? der : (x - b >= a ? lin : dir);
+}
+__device__ __forceinline__ float dvol_fast(float a, float b, float c, float S, float alpha) {
+    if (alpha <= 0.f || alpha >= S) return 0.f;
+    const float x = 2.f * alpha > S ? S - alpha : alpha;  // the area is symmetric
+    return (vdf2(x, a, b) - vdf2(x - c, a, b)) / (2.f * c);
+}
+
 // The same with the reciprocals of one normal taken once (many plane
 // constants per normal): ia = 1/a, ib = 1/b, i6c = 1/(6c); a product
 // replaces each division (results within a few ulp of vol_fast's).
@@ -279,11 +298,18 @@ __device__ __noinline__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr
             }
         }
     }
-    // polish on the exact piecewise form
+    // polish on the exact piecewise form (FP32: its branch-free evaluation)
     T S = a + b + c;
-    T dv = dvol_sorted(a, b, c, al);
+    T dv, vv;
+    if constexpr (std::is_same<T, float>::value) {
+        dv = dvol_fast(a, b, c, S, al);
+        vv = vol_fast(a, b, c, S, al);
+    } else {
+        dv = dvol_sorted(a, b, c, al);
+        vv = dv > T(0) ? vol_sorted(a, b, c, al) : T(0);
+    }
     if (dv > T(0)) {
-        T nal = al - (vol_sorted(a, b, c, al) - v) / dv;
+        T nal = al - (vv - v) / dv;
         if (nal > T(0) && nal <= T(0.5) * S) al = nal;
     }
     if (region) *region = reg;
