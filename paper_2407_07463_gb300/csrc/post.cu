@@ -49,73 +49,94 @@ __global__ void k_moving_bits(const int* __restrict__ labels, Dims g, MoveTables
     }
 }
 
-// For every cell of a moving drop m: the fields (other than its own) with an
-// occupied cell within Chebyshev distance `reach`, and the other moving
-// drops with a cell within that distance.  Only cells on the drop's boundary
-// (a 26-neighbour outside the drop) scan the (2 reach + 1)^3 box: walking
-// from an interior cell towards any cell outside the drop reaches a boundary
-// cell that is no farther from it.  Interior cells test their own position.
-// Rows of the box are read as bit windows of the occupancy planes.
-__global__ void k_touch(const int* __restrict__ labels, const uint32_t* __restrict__ bits,
-                        const uint32_t* __restrict__ mvbits, Dims g, int n_active, int reach, MoveTables mt,
-                        const int* __restrict__ mv_fields, int n_mv_fields, unsigned* __restrict__ touch,
-                        unsigned* __restrict__ conflict, int Mw) {
-    long long total = (long long)n_mv_fields * g.N;
-    long long per_field_words = (long long)g.rows * g.W;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int fi = (int)(t / g.N);
-        int x = (int)(t - (long long)fi * g.N);
-        int i, j, k;
-        decode(x, g, i, j, k);
-        if (!bit_at(mvbits + (size_t)fi * per_field_words, g.W, k * g.ny + j, i)) continue;
-        int f = mv_fields[fi];
-        const int* lab = labels + (size_t)f * g.N;
-        int l = lab[x];
-        int m = moving_index(mt, f, l);
-        if (m < 0) continue;
-        bool interior = true;
-        for (int dz = -1; dz <= 1 && interior; ++dz)
-            for (int dy = -1; dy <= 1 && interior; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (lab[cell(wrapi(i + dx, g.nx), wrapi(j + dy, g.ny), wrapi(k + dz, g.nz), g)] != l) {
-                        interior = false;
-                        break;
+// 64 consecutive occupancy bits of a row starting at cell x0 (periodic).
+__device__ __forceinline__ unsigned long long row_window64(const uint32_t* __restrict__ row, int W, int nx, int x0) {
+    return (unsigned long long)row_window(row, W, nx, x0) |
+           ((unsigned long long)row_window(row, W, nx, x0 + 32) << 32);
+}
+
+// For every moving drop m: the fields (other than its own) with an occupied
+// cell within Chebyshev distance `reach` of a cell of m (touch[m], a field
+// mask), and the other moving drops within that distance (conflict[m], a
+// bit per moving drop).  One warp takes one 32-cell word of a moving-drop
+// bit plane at a time; the set bits of the word are grouped by drop, each
+// group is dilated along x by `reach` inside a 64-cell frame starting at
+// the word's first cell minus `reach`, and the lanes share the
+// (2 reach + 1)^2 rows of the window, reading each row of every field as a
+// 64-bit window of its occupancy bits (reach <= 16).
+__global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ labels,
+                                                     const uint32_t* __restrict__ bits,
+                                                     const uint32_t* __restrict__ mvbits, Dims g, int n_active,
+                                                     int reach, MoveTables mt, const int* __restrict__ mv_fields,
+                                                     int n_mv_fields, unsigned* __restrict__ touch,
+                                                     unsigned* __restrict__ conflict, int Mw) {
+    const int lane = threadIdx.x & 31;
+    const long long per_field = (long long)g.rows * g.W;
+    const long long words = (long long)n_mv_fields * per_field;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int span = 2 * reach + 1, nrows = span * span;
+    for (long long base = warp * 32; base < words; base += nwarps * 32) {
+        // 32 words per round, one per lane; then every non-empty one in turn
+        const long long my = base + lane;
+        const uint32_t mine = my < words ? mvbits[my] : 0u;
+        unsigned todo = __ballot_sync(0xffffffffu, mine != 0u);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const long long wd = base + src;
+            const uint32_t word = __shfl_sync(0xffffffffu, mine, src);
+            const int q = (int)(wd / per_field);
+            const long long rem = wd - (long long)q * per_field;
+            const int row = (int)(rem / g.W);
+            const int wi = (int)(rem - (long long)row * g.W);
+            const int j = row % g.ny, k = row / g.ny;
+            const int f = mv_fields[q];
+            const int* lab = labels + (size_t)f * g.N + (size_t)row * g.nx;
+            // the moving drop of each set bit
+            const bool set = (word >> lane) & 1u;
+            const int m_lane = set ? moving_index(mt, f, lab[wi * 32 + lane]) : -1;
+            unsigned rest = __ballot_sync(0xffffffffu, set);
+            while (rest) {
+                const int lead = __ffs(rest) - 1;
+                const int m = __shfl_sync(0xffffffffu, m_lane, lead);
+                const unsigned grp = __ballot_sync(0xffffffffu, set && m_lane == m);
+                rest &= ~grp;
+                if (m < 0) continue;
+                // frame bit c <-> cell 32 wi - reach + c; cells within reach
+                // along x of the group's cells
+                unsigned long long dil = 0;
+                for (int s2 = 0; s2 <= 2 * reach; ++s2) dil |= (unsigned long long)grp << s2;
+                const int x0 = wi * 32 - reach;
+                unsigned tmask = 0;
+                for (int r2 = lane; r2 < nrows; r2 += 32) {
+                    const int dz = r2 / span - reach, dy = r2 % span - reach;
+                    const int kk = wrapi(k + dz, g.nz), jj = wrapi(j + dy, g.ny);
+                    const size_t roff = (size_t)(kk * g.ny + jj) * g.W;
+                    for (int n = 0; n < n_active; ++n) {
+                        if (n == f || ((tmask >> n) & 1u)) continue;
+                        if (row_window64(bits + (size_t)n * per_field + roff, g.W, g.nx, x0) & dil) tmask |= 1u << n;
+                    }
+                    for (int q2 = 0; q2 < n_mv_fields; ++q2) {
+                        unsigned long long wv = row_window64(mvbits + (size_t)q2 * per_field + roff, g.W, g.nx, x0) & dil;
+                        const int f2 = mv_fields[q2];
+                        while (wv) {
+                            const int b = __ffsll((long long)wv) - 1;
+                            wv &= wv - 1ull;
+                            const int y = cell(wrapi(x0 + b, g.nx), jj, kk, g);
+                            const int l2 = labels[(size_t)f2 * g.N + y];
+                            const int m2 = moving_index(mt, f2, l2);
+                            if (m2 < 0 || m2 == m) continue;
+                            const unsigned bitm = 1u << (m2 & 31);
+                            unsigned* wd2 = conflict + (size_t)m * Mw + (m2 >> 5);
+                            if (!(*wd2 & bitm)) atomicOr(wd2, bitm);
+                        }
                     }
                 }
-        int r = interior ? 0 : reach;
-        int span = 2 * r + 1;
-        uint32_t smask = span >= 32 ? 0xffffffffu : ((1u << span) - 1u);
-        unsigned tmask = 0;
-        for (int dz = -r; dz <= r; ++dz) {
-            int kk = wrapi(k + dz, g.nz);
-            for (int dy = -r; dy <= r; ++dy) {
-                int jj = wrapi(j + dy, g.ny);
-                size_t row = (size_t)(kk * g.ny + jj) * g.W;
-                for (int n = 0; n < n_active; ++n) {
-                    if (n == f || ((tmask >> n) & 1u)) continue;
-                    if (row_window(bits + (size_t)n * per_field_words + row, g.W, g.nx, i - r) & smask)
-                        tmask |= 1u << n;
-                }
-                for (int q = 0; q < n_mv_fields; ++q) {
-                    uint32_t wv = row_window(mvbits + (size_t)q * per_field_words + row, g.W, g.nx, i - r) & smask;
-                    int f2 = mv_fields[q];
-                    while (wv) {
-                        int b = __ffs(wv) - 1;
-                        wv &= wv - 1u;
-                        int y = cell(wrapi(i - r + b, g.nx), jj, kk, g);
-                        int l2 = labels[(size_t)f2 * g.N + y];
-                        if (f2 == f && l2 == l) continue;
-                        int m2 = moving_index(mt, f2, l2);
-                        if (m2 < 0 || m2 == m) continue;
-                        unsigned bitm = 1u << (m2 & 31);
-                        unsigned* wd = conflict + (size_t)m * Mw + (m2 >> 5);
-                        if (!(*wd & bitm)) atomicOr(wd, bitm);
-                    }
-                }
+                tmask = __reduce_or_sync(0xffffffffu, tmask);
+                if (lane == 0 && tmask) atomicOr(touch + m, tmask);
             }
         }
-        if (tmask) atomicOr(touch + m, tmask);
     }
 }
 
@@ -124,9 +145,9 @@ cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mv
                            unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st) {
     long long words = (long long)n_mv_fields * g.rows * g.W;
     k_moving_bits<<<grid_for(words * 32, 256), 256, 0, st>>>(labels, g, mt, mv_fields, n_mv_fields, mvbits);
-    long long total = (long long)n_mv_fields * g.N;
-    k_touch<<<grid_for(total, 128), 128, 0, st>>>(labels, bits, mvbits, g, n_active, reach, mt, mv_fields,
-                                                   n_mv_fields, touch, conflict, Mw);
+    if (reach > 16) return cudaErrorInvalidValue;  // the 64-cell frame holds 32 + 2 reach cells
+    k_touch_words<<<grid_for(words, 256), 256, 0, st>>>(labels, bits, mvbits, g, n_active, reach, mt, mv_fields,
+                                                         n_mv_fields, touch, conflict, Mw);
     return cudaGetLastError();
 }
 
