@@ -289,6 +289,39 @@ __global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__
     if (root) rank[x] = warp_tot[wid] + __popc(m & ((1u << lane) - 1u));
 }
 
+// The same for rows of whole 32-cell words (bit word gw holds cells
+// 32 gw .. 32 gw + 31): one warp per 1024-cell block, a lane per word, and
+// only the occupied cells read their parent.
+__global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restrict__ bits_f,
+                                                         const int* __restrict__ parent, int* __restrict__ rank,
+                                                         int* __restrict__ block_tot, int nblk, long long words) {
+    const int lane = threadIdx.x & 31;
+    const int rb = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (rb >= nblk) return;  // whole warps leave together
+    const long long gw = (long long)rb * 32 + lane;
+    uint32_t m = gw < words ? bits_f[gw] : 0u, rm = 0u;
+    const int x0 = (int)(gw * 32);
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        if (parent[x0 + b] == x0 + b) rm |= 1u << b;
+    }
+    const int cnt = __popc(rm);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) block_tot[rb] = incl;
+    int r = incl - cnt;
+    while (rm) {
+        const int b = __ffs(rm) - 1;
+        rm &= rm - 1u;
+        rank[x0 + b] = r++;
+    }
+}
+
 // Exclusive scan of n block totals in one block; off[n] = total.
 __global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ tot, int* __restrict__ off,
                                                       int n, int* total_out) {
@@ -385,6 +418,39 @@ cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, 
     return cudaGetLastError();
 }
 
+// Labels for rows of whole 32-cell words: a thread per word writes its 32
+// labels as eight 16-byte stores; occupied cells take 1 + the global rank
+// of their root.
+__global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __restrict__ bits_f,
+                                                           const int* __restrict__ parent,
+                                                           const int* __restrict__ rank, const int* __restrict__ off,
+                                                           int* __restrict__ label, int* __restrict__ root_of,
+                                                           int root_cap, long long words) {
+    for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
+         gw += (long long)gridDim.x * blockDim.x) {
+        const uint32_t w = bits_f[gw];
+        const int x0 = (int)(gw * 32);
+        int4* dst = reinterpret_cast<int4*>(label + x0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int l4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int b = 4 * q + e;
+                int l = 0;
+                if ((w >> b) & 1u) {
+                    const int x = x0 + b;
+                    const int r = parent[x];
+                    l = off[r >> 10] + rank[r] + 1;
+                    if (r == x && root_of && l <= root_cap) root_of[l - 1] = x;
+                }
+                l4[e] = l;
+            }
+            dst[q] = make_int4(l4[0], l4[1], l4[2], l4[3]);
+        }
+    }
+}
+
 // Labels of one row segment per warp: 0 for empty cells, 1 + rank of the
 // root for occupied ones.
 __global__ void k_ccl_relabel(const uint32_t* __restrict__ bits_f, const int* __restrict__ parent,
@@ -422,10 +488,19 @@ cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* pa
         k_ccl_merge26<<<grid_for(g.N, 256), 256, 0, st>>>(bits_f, parent, g);
     }
     k_ccl_flatten<<<bw, 256, 0, st>>>(bits_f, parent, g);
-    k_ccl_count<<<nb, 1024, 0, st>>>(bits_f, parent, rank, block_tot, g);
+    // rows of whole words (and a 16-byte-aligned label array): word-wise passes
+    const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)label & 15) == 0;
+    if (wordwise)
+        k_ccl_count_words<<<(nb + 7) / 8, 256, 0, st>>>(bits_f, parent, rank, block_tot, nb, words);
+    else
+        k_ccl_count<<<nb, 1024, 0, st>>>(bits_f, parent, rank, block_tot, g);
     k_scan_blocks<<<1, 1024, 0, st>>>(block_tot, block_off, nb, n_out);
-    k_ccl_relabel<<<grid_for(words * 32, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
-                                                             root_cap, g);
+    if (wordwise)
+        k_ccl_relabel_words<<<grid_for(words, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
+                                                                  root_cap, words);
+    else
+        k_ccl_relabel<<<grid_for(words * 32, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
+                                                                 root_cap, g);
     if (launches) *launches += 6;
     return cudaGetLastError();
 }

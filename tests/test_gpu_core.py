@@ -249,7 +249,7 @@ def test_cfl_and_nonfinite_errors(vof):
 
 
 @pytest.mark.parametrize("conn", [6, 26])
-@pytest.mark.parametrize("shape", [(16, 16, 32), (9, 13, 48), (5, 7, 70)])
+@pytest.mark.parametrize("shape", [(16, 16, 32), (9, 13, 48), (5, 7, 70), (11, 3, 96), (40, 33, 64)])
 def test_label_bit_exact(vof, shape, conn):
     rng = np.random.default_rng(sum(shape) + conn)
     c = rng.random(shape) * (rng.random(shape) < 0.35)
