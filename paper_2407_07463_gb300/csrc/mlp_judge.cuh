@@ -37,9 +37,23 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
     sort3(a, b, c);
     const VolRecip r = vol_recip(a, b, c);
+    // first pass: the cells the plane leaves whole (volume 0 or 1) cost a
+    // compare; the cut ones are collected in a mask and take the volume in a
+    // second pass (about a third of the 27 for a plane through the centre)
     float e = 0.f;
-#pragma unroll 3
+    uint32_t cut = 0u;
+#pragma unroll
     for (int q = 0; q < 27; ++q) {
+        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
+        const float aq = al + off - (m0 * i + m1 * j + m2 * k);
+        if (aq > 0.f && aq < r.S)
+            cut |= 1u << q;
+        else
+            e += fabsf((aq <= 0.f ? 0.f : 1.f) - st[q * STRIDE]);
+    }
+    while (cut) {
+        const int q = __ffs(cut) - 1;
+        cut &= cut - 1u;
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
         const float v = vol_fast_r(r, al + off - (m0 * i + m1 * j + m2 * k));
         e += fabsf(v - st[q * STRIDE]);
