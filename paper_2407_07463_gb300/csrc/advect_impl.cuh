@@ -281,7 +281,7 @@ SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
         r.wpb = a.update_warps > 0 ? a.update_warps : 8;
         int per_sm = a.update_blocks_per_sm;
         if (per_sm <= 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB>, 32 * r.wpb, 0) !=
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB, 1>, 32 * r.wpb, 0) !=
                  cudaSuccess ||
              per_sm < 1))
             per_sm = 1;
@@ -365,8 +365,7 @@ cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
             face_fluxes(S, d, sw, lists[cur], G.cap, G.gb, a);
             if (a.prof) a.prof->begin(P_UPDATE);
             if (vec) {
-                k_update_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, d, dn, sw, tau, lists[nxt], G.cap,
-                                                                      counts[nxt]);
+                launch_update_bx(S, d, dn, sw, tau, lists[nxt], G.cap, counts[nxt], G.gb, 32 * G.wpb, a.stream);
             } else {
                 const T* ins[3] = {B0.c, B0.b1, B0.b2};
                 T* outs[3] = {B0.b1, B0.b2, B0.c};
@@ -399,7 +398,7 @@ cudaError_t advect_first_sweep(const BoxSet<T, NB>& S, SweepArgs& a) {
     k_list_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, lists[0], G.cap, counts[0]);
     scan_face_counts(counts[0], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
     face_fluxes(S, rot, 0, lists[0], G.cap, G.gb, a);
-    k_update_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, dn, 0, (T)a.tau, lists[1], G.cap, counts[1]);
+    launch_update_bx(S, rot, dn, 0, (T)a.tau, lists[1], G.cap, counts[1], G.gb, 32 * G.wpb, a.stream);
     return cudaGetLastError();
 }
 

@@ -305,9 +305,9 @@ vof_status vof_batch_init(const vof_batch_config* cfg, const vof_box_desc* boxes
     {
         int occ = 0;
         if (fp64_batch(cfg))
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1>, 256, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1>, 256, 0);
         if (occ > 0) B->update_blocks_per_sm = occ;
         (void)cudaGetLastError();
     }
@@ -374,9 +374,9 @@ vof_status vof_batch_tune(vof_batch* B) {
     for (int w : warps_c) {
         int occ = 0;
         if (B->cfg.precision == VOF_FP64)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes>, 32 * w, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1>, 32 * w, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes>, 32 * w, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1>, 32 * w, 0);
         for (int p = 1; p <= std::max(1, occ); p = p < 2 ? 2 : p + 2) {
             const float ms = time_shape(B, w, p, 3);
             ++n;

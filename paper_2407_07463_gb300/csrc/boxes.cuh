@@ -195,15 +195,15 @@ __global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
 }
 
-// Update pass of sweep `sweep` along d for every box (see k_update for the
+// Update pass of sweep PH (0, 1, 2) along d for every box (see k_update for the
 // arithmetic): c_out = c_in - (F_hi - F_lo) + c_c (s_hi - s_lo), c_c bits
 // written in sweep 0 and read after, the clip and the occupancy bits in
 // sweep 2, and the faces of the next sweep (direction dn) whose donor is
 // interfacial appended to the block's list segment.
-template <typename T, int NB>
+template <typename T, int NB, int PH>
 __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSet<T, NB> S, int d, int dn,
-                                                   int sweep, T tau, unsigned long long* __restrict__ nlist,
-                                                   long long cap, int* __restrict__ ncounts) {
+                                                   T tau, unsigned long long* __restrict__ nlist, long long cap,
+                                                   int* __restrict__ ncounts) {
     constexpr int VW = VecOf<T>::W;
     __shared__ int s_count;
     if (threadIdx.x == 0) s_count = 0;
@@ -218,17 +218,20 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
         const ItemCells ic = item_cells(B, it - B.item0, lane);
         const int x0 = ic.x0, i0 = ic.i0, f = ic.f;
         const size_t base = (size_t)f * g.N;
-        const T* __restrict__ cf = sweep_in(B, sweep) + base;
-        T* __restrict__ co = sweep_out(B, sweep) + base;
+        const T* __restrict__ cf = sweep_in(B, PH) + base;
+        T* __restrict__ co = sweep_out(B, PH) + base;
         const T* __restrict__ ud = B.u + (size_t)d * g.N;
         const T* __restrict__ udn = B.u + (size_t)dn * g.N;
-        const T* __restrict__ flux = B.flux;
+        const T* __restrict__ flux = B.flux + base;
         const int hi_d = d == 1 ? ic.hi_y : ic.hi_z, lo_d = d == 1 ? ic.lo_y : ic.lo_z;
         const int hi_dn = dn == 1 ? ic.hi_y : ic.hi_z;
         T cx[VW], ulo[VW], uhi[VW], cl[VW], ch[VW], unl[VW], unh[VW];
         ld16(cf + x0, cx);
         ld16(ud + x0, ulo);
         ld16(udn + x0, unl);
+        // offset from the lane's first cell to the high neighbour along x of
+        // its last (periodic in the row)
+        int xh_last = VW;
         if (d == 0) {
             const T cprev = prev_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
             const T cnext = next_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
                 ch[e] = e == VW - 1 ? cnext : cx[e + 1];
                 uhi[e] = e == VW - 1 ? unext : ulo[e + 1];
             }
+            xh_last = i0 + VW == g.nx ? VW - g.nx : VW;
         } else {
             ld16(cf + x0 + lo_d, cl);
             ld16(cf + x0 + hi_d, ch);
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
         const int sh_bits = (lane * VW) & 31;
         const bool leader = ic.valid && (lane & (32 / VW - 1)) == 0;
         uint32_t ccm = 0;
-        if (sweep == 0) {
+        if (PH == 0) {
             if (ic.valid) {
 #pragma unroll
                 for (int e = 0; e < VW; ++e) ccm |= (above_half(cx[e]) ? 1u : 0u) << e;
@@ -266,35 +270,34 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
         } else {
             ccm = (B.ccbits[word] >> sh_bits) & ((1u << VW) - 1u);
         }
-        T v[VW];
+        T v[VW], rem[VW];
         uint32_t occm = 0, flo = 0, fhi = 0;
+        bool clipped = false;
         int nflag = 0;
-        double removed = 0.0;
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-            const int x = x0 + e;
             const int sl = vsign(ulo[e]), sh = vsign(uhi[e]);
             const int kl = sl == 0 ? 0 : vclass(sl > 0 ? cl[e] : cx[e]);
             const int kh = sh == 0 ? 0 : vclass(sh < 0 ? ch[e] : cx[e]);
             const bool cc = (ccm >> e) & 1u;
-            T ve;
-            if (kl == 0 && kh == 0 && !cc && is_exact_zero(cx[e])) {
-                ve = cx[e];
-            } else {
-                const int xh = d == 0 ? (e < VW - 1 ? x + 1 : (i0 + VW == g.nx ? x0 + VW - g.nx : x0 + VW))
-                                      : x + hi_d;
-                const T s_lo = ulo[e] * B.sfac, s_hi = uhi[e] * B.sfac;
-                const T F_lo = kl == 0 ? T(0) : (kl == 2 ? s_lo : flux[base + x]);
-                const T F_hi = kh == 0 ? T(0) : (kh == 2 ? s_hi : flux[base + xh]);
-                ve = cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi - s_lo);
-                if (sweep == 2 && (ve < T(0) || ve > T(1))) {
-                    const T cl0 = ve < T(0) ? T(0) : T(1);
-                    if (ic.valid) removed += (double)ve - (double)cl0;
-                    ve = cl0;
-                }
+            const T s_lo = ulo[e] * B.sfac, s_hi = uhi[e] * B.sfac;
+            T F_lo = kl == 2 ? s_lo : T(0), F_hi = kh == 2 ? s_hi : T(0);
+            if (kl == 1) F_lo = flux[x0 + e];
+            if (kh == 1) F_hi = flux[x0 + (d == 0 ? (e < VW - 1 ? e + 1 : xh_last) : e + hi_d)];
+            // a cell that nothing enters or leaves keeps its bits (signed zero)
+            T ve = (kl | kh) == 0 && !cc ? cx[e] : cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi - s_lo);
+            rem[e] = T(0);
+            if (PH == 2) {
+                const bool clip = ve < T(0) || ve > T(1);
+                const T cl0 = ve < T(0) ? T(0) : T(1);
+                // ve - cl0 is exact (Sterbenz), so the FP64 sum below sees
+                // the same terms as a sum of FP64 differences
+                rem[e] = clip && ic.valid ? ve - cl0 : T(0);
+                clipped |= clip && ic.valid;
+                ve = clip ? cl0 : ve;
+                if (ic.valid && ve > tau) occm |= 1u << e;
             }
             v[e] = ve;
-            if (ic.valid && sweep == 2 && ve > tau) occm |= 1u << e;
             const bool interf = ic.valid && vclass(ve) == 1;
             if (interf && vsign(unl[e]) < 0) {
                 flo |= 1u << e;
@@ -306,10 +309,13 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
             }
         }
         if (ic.valid) st16(co + x0, v);
-        if (sweep == 2) {
+        if (PH == 2) {
             const uint32_t w = gather_word<VW>(occm, lane);
             if (leader) B.occbits[word] = w;
-            if (__any_sync(0xffffffffu, removed != 0.0)) {
+            if (__any_sync(0xffffffffu, clipped)) {
+                double removed = 0.0;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) removed += (double)rem[e];
                 for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
                 if (lane == 0 && removed != 0.0) atomicAdd(B.clipped + f, removed);
             }
@@ -332,6 +338,18 @@ __global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSe
     }
     __syncthreads();
     if (threadIdx.x == 0) ncounts[blockIdx.x] = s_count;
+}
+
+// Launch of the update pass of sweep `sweep` (0, 1, 2).
+template <typename T, int NB>
+inline void launch_update_bx(const BoxSet<T, NB>& S, int d, int dn, int sweep, T tau, unsigned long long* nlist,
+                             long long cap, int* ncounts, int gb, int threads, cudaStream_t st) {
+    if (sweep == 0)
+        k_update_bx<T, NB, 0><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+    else if (sweep == 1)
+        k_update_bx<T, NB, 1><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+    else
+        k_update_bx<T, NB, 2><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
 }
 
 // A listed face of a box set: box, field, the cell x of the face's high
