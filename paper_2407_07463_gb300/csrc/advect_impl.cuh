@@ -281,14 +281,20 @@ SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
         r.wpb = a.update_warps > 0 ? a.update_warps : 8;
         int per_sm = a.update_blocks_per_sm;
         if (per_sm <= 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB, 1>, 32 * r.wpb, 0) !=
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB, 1, false>, 32 * r.wpb, 0) !=
                  cudaSuccess ||
              per_sm < 1))
             per_sm = 1;
         r.gb = std::max(1, std::min(152 * per_sm, kListBlocks / std::max(1, r.wpb / 8)));
         r.gb = std::min(r.gb, (S.items + r.wpb - 1) / r.wpb);
         r.gb = std::max(r.gb, 1);
-        const long long per_warp = ((long long)S.items + (long long)r.gb * r.wpb - 1) / ((long long)r.gb * r.wpb);
+        // a warp of the listing pass takes items (one field of a row chunk),
+        // one of the update pass row chunks with every field
+        const long long warps = (long long)r.gb * r.wpb;
+        int kmax = 1;
+        for (int b = 0; b < S.n; ++b) kmax = std::max(kmax, S.b[b].K);
+        const long long per_warp = std::max(((long long)S.items + warps - 1) / warps,
+                                            kmax * (((long long)S.chunks + warps - 1) / warps));
         r.cap = 2LL * CH * r.wpb * per_warp;
     } else {
         const Dims& g = S.b[0].g;

@@ -488,6 +488,7 @@ static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
     B.g = g;
     B.K = ctx->n_active;
     B.item0 = 0;
+    B.chunk0 = 0;
     B.cpr = (g.nx + CH - 1) / CH;
     B.divK = fastdiv_make((uint32_t)B.K);
     B.divcpr = fastdiv_make((uint32_t)B.cpr);
@@ -504,6 +505,7 @@ static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
     B.clipped = clipped;
     S.n = 1;
     S.items = B.K * g.rows * B.cpr;
+    S.chunks = g.rows * B.cpr;
     return S;
 }
 

@@ -59,7 +59,7 @@ BatchLayout batch_layout(const vof_batch_config* cfg, const vof_box_desc* boxes,
     const size_t es = cfg->precision == VOF_FP64 ? 8 : 4;
     const int CH = (int)(512 / es);
     size_t o = 0;
-    long long items = 0;
+    long long items = 0, chunks = 0, kmax = 1;
     for (int b = 0; b < n; ++b) {
         const vof_box_desc& d = boxes[b];
         const size_t N = (size_t)d.nx * d.ny * d.nz, K = (size_t)d.k_capacity;
@@ -71,9 +71,13 @@ BatchLayout batch_layout(const vof_batch_config* cfg, const vof_box_desc* boxes,
         L.ccbits.push_back(o), o = al256(o + K * words * 4);
         L.occbits.push_back(o), o = al256(o + K * words * 4);
         items += (long long)d.k_capacity * d.ny * d.nz * ((d.nx + CH - 1) / CH);
+        chunks += (long long)d.ny * d.nz * ((d.nx + CH - 1) / CH);
+        kmax = std::max<long long>(kmax, d.k_capacity);
     }
     L.items = items;
-    L.list_entries = 2LL * CH * (items + 8LL * kListBlocks);
+    // a warp of the update pass lists up to 2 faces per cell of every field
+    // of each of its row chunks
+    L.list_entries = 2LL * CH * kmax * (chunks + 8LL * kListBlocks);
     L.tile_cap = (int)std::min<long long>((L.list_entries + kFaceTile - 1) / kFaceTile, INT32_MAX);
     L.clipped = o, o = al256(o + (size_t)n * 16 * 8);
     L.list = o, o = al256(o + 2 * (size_t)L.list_entries * 8);
@@ -113,7 +117,7 @@ template <typename T>
 BoxSet<T, kMaxBoxes> batch_set(vof_batch* B) {
     BoxSet<T, kMaxBoxes> S;
     const int CH = 32 * VecOf<T>::W;
-    int item = 0;
+    int item = 0, chunk = 0;
     S.n = (int)B->boxes.size();
     for (int b = 0; b < S.n; ++b) {
         const vof_box_desc& d = B->boxes[b];
@@ -121,6 +125,7 @@ BoxSet<T, kMaxBoxes> batch_set(vof_batch* B) {
         X.g = make_dims(d.nx, d.ny, d.nz);
         X.K = d.k_active;
         X.item0 = item;
+        X.chunk0 = chunk;
         X.cpr = (d.nx + CH - 1) / CH;
         X.divK = fastdiv_make((uint32_t)X.K);
         X.divcpr = fastdiv_make((uint32_t)X.cpr);
@@ -136,8 +141,10 @@ BoxSet<T, kMaxBoxes> batch_set(vof_batch* B) {
         X.occbits = (uint32_t*)(B->ws + B->L.occbits[b]);
         X.clipped = (double*)(B->ws + B->L.clipped) + 16 * b;
         item += X.K * X.g.rows * X.cpr;
+        chunk += X.g.rows * X.cpr;
     }
     S.items = item;
+    S.chunks = chunk;
     return S;
 }
 
@@ -305,9 +312,9 @@ vof_status vof_batch_init(const vof_batch_config* cfg, const vof_box_desc* boxes
     {
         int occ = 0;
         if (fp64_batch(cfg))
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1, false>, 256, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1, false>, 256, 0);
         if (occ > 0) B->update_blocks_per_sm = occ;
         (void)cudaGetLastError();
     }
@@ -374,9 +381,9 @@ vof_status vof_batch_tune(vof_batch* B) {
     for (int w : warps_c) {
         int occ = 0;
         if (B->cfg.precision == VOF_FP64)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1>, 32 * w, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1, false>, 32 * w, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1>, 32 * w, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1, false>, 32 * w, 0);
         for (int p = 1; p <= std::max(1, occ); p = p < 2 ? 2 : p + 2) {
             const float ms = time_shape(B, w, p, 3);
             ++n;

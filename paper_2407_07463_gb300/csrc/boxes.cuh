@@ -53,6 +53,7 @@ struct BoxDev {
     Dims g;
     int K;      // fields advected
     int item0;  // first work item of the box
+    int chunk0; // first row chunk of the box (the update pass's unit: every field of it)
     int cpr;    // row chunks per row, ceil(nx / (32 VW))
     FastDiv divK, divcpr, divny;  // by K, cpr and ny
     T sfac;     // dt / h
@@ -71,7 +72,8 @@ struct BoxDev {
 template <typename T, int NB>
 struct BoxSet {
     int n;
-    int items;
+    int items;   // row chunk x field, over every box
+    int chunks;  // row chunks, over every box
     BoxDev<T> b[NB];
 };
 
@@ -87,6 +89,18 @@ __device__ __forceinline__ int box_of_item(const BoxSet<T, NB>& S, int it) {
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (S.b[mid].item0 <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ int box_of_chunk(const BoxSet<T, NB>& S, int ch) {
+    if (NB == 1) return 0;
+    int lo = 0, hi = S.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.b[mid].chunk0 <= ch) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -108,13 +122,13 @@ struct ItemCells {
     int lo_y, hi_y, lo_z, hi_z;
 };
 
+// Geometry of row chunk `chunk` of a box for lane `lane` (f = 0).
 template <typename T>
-__device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, int lane) {
+__device__ __forceinline__ ItemCells chunk_cells(const BoxDev<T>& B, int chunk, int lane) {
     constexpr int VW = VecOf<T>::W;
     const Dims& g = B.g;
     ItemCells r;
-    const int chunk = (int)fastdiv((uint32_t)local, B.divK);
-    r.f = local - chunk * B.K;
+    r.f = 0;
     r.row = (int)fastdiv((uint32_t)chunk, B.divcpr);
     const int seg = chunk - r.row * B.cpr;
     const int i0 = seg * 32 * VW + lane * VW;
@@ -130,6 +144,15 @@ __device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, i
     r.hi_y = r.j == g.ny - 1 ? -(g.ny - 1) * g.nx : g.nx;
     r.lo_z = r.k == 0 ? (g.nz - 1) * plane : -plane;
     r.hi_z = r.k == g.nz - 1 ? -(g.nz - 1) * plane : plane;
+    return r;
+}
+
+// Geometry of item `local` (row chunk x field) of a box for lane `lane`.
+template <typename T>
+__device__ __forceinline__ ItemCells item_cells(const BoxDev<T>& B, int local, int lane) {
+    const int chunk = (int)fastdiv((uint32_t)local, B.divK);
+    ItemCells r = chunk_cells(B, chunk, lane);
+    r.f = local - chunk * B.K;
     return r;
 }
 
@@ -195,161 +218,246 @@ __global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
 }
 
-// Update pass of sweep PH (0, 1, 2) along d for every box (see k_update for the
-// arithmetic): c_out = c_in - (F_hi - F_lo) + c_c (s_hi - s_lo), c_c bits
-// written in sweep 0 and read after, the clip and the occupancy bits in
-// sweep 2, and the faces of the next sweep (direction dn) whose donor is
+// One field's loads of a row chunk in the update pass: the lane's VW
+// cells, and either its neighbours along d (d = 1, 2) or the two values
+// beyond its ends along x that the lanes at the warp's or the row's ends
+// read from memory (d = 0); the c_c bit word from sweep 1 on.
+template <typename T>
+struct FieldRow {
+    static constexpr int VW = VecOf<T>::W;
+    T cx[VW], cl[VW], ch[VW];
+    T pv, nv;
+    uint32_t ccw;
+};
+
+template <typename T, int PH, bool DX>
+__device__ __forceinline__ void load_field_row(FieldRow<T>& r, const T* __restrict__ cf, int x0, int lo_d,
+                                               int hi_d, bool need_prev, int xp, bool need_next, int xn,
+                                               const uint32_t* __restrict__ ccw) {
+    ld16(cf + x0, r.cx);
+    if (DX) {
+        r.pv = need_prev ? cf[xp] : T(0);
+        r.nv = need_next ? cf[xn] : T(0);
+    } else {
+        ld16(cf + x0 + lo_d, r.cl);
+        ld16(cf + x0 + hi_d, r.ch);
+    }
+    r.ccw = PH == 0 ? 0u : *ccw;
+}
+
+// Update pass of sweep PH (0, 1, 2) along d (DX: d == 0) for every box (see k_update for
+// the arithmetic): c_out = c_in - (F_hi - F_lo) + c_c (s_hi - s_lo), c_c
+// bits written in sweep 0 and read after, the clip and the occupancy bits
+// in sweep 2, and the faces of the next sweep (direction dn) whose donor is
 // interfacial appended to the block's list segment.
-template <typename T, int NB, int PH>
-__global__ void __launch_bounds__(256) k_update_bx(const __grid_constant__ BoxSet<T, NB> S, int d, int dn,
-                                                   T tau, unsigned long long* __restrict__ nlist, long long cap,
-                                                   int* __restrict__ ncounts) {
+//
+// A warp takes one 32 * VW-cell row chunk and walks every field of it: the
+// geometry, the velocities and their signs are taken once per chunk, and
+// the loads of the next field are issued before the current one is
+// updated.
+template <typename T, int NB, int PH, bool DX>
+__global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ BoxSet<T, NB> S, int d, int dn,
+                                                      T tau, unsigned long long* __restrict__ nlist,
+                                                      long long cap, int* __restrict__ ncounts) {
     constexpr int VW = VecOf<T>::W;
     __shared__ int s_count;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
+    const int sh_bits = (lane * VW) & 31;
     unsigned long long* seg = nlist + (size_t)blockIdx.x * cap;
-    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < S.items; it += gridDim.x * wpb) {
-        const int bx = box_of_item(S, it);
+    for (int chk = blockIdx.x * wpb + (threadIdx.x >> 5); chk < S.chunks; chk += gridDim.x * wpb) {
+        const int bx = box_of_chunk(S, chk);
         const BoxDev<T>& B = S.b[bx];
         const Dims& g = B.g;
-        const ItemCells ic = item_cells(B, it - B.item0, lane);
-        const int x0 = ic.x0, i0 = ic.i0, f = ic.f;
-        const size_t base = (size_t)f * g.N;
-        const T* __restrict__ cf = sweep_in(B, PH) + base;
-        T* __restrict__ co = sweep_out(B, PH) + base;
-        const T* __restrict__ ud = B.u + (size_t)d * g.N;
-        const T* __restrict__ udn = B.u + (size_t)dn * g.N;
-        const T* __restrict__ flux = B.flux + base;
+        const ItemCells ic = chunk_cells(B, chk - B.chunk0, lane);
+        const int x0 = ic.x0, i0 = ic.i0;
         const int hi_d = d == 1 ? ic.hi_y : ic.hi_z, lo_d = d == 1 ? ic.lo_y : ic.lo_z;
-        const int hi_dn = dn == 1 ? ic.hi_y : ic.hi_z;
-        T cx[VW], ulo[VW], uhi[VW], cl[VW], ch[VW], unl[VW], unh[VW];
-        ld16(cf + x0, cx);
-        ld16(ud + x0, ulo);
-        ld16(udn + x0, unl);
-        // offset from the lane's first cell to the high neighbour along x of
-        // its last (periodic in the row)
-        int xh_last = VW;
-        if (d == 0) {
-            const T cprev = prev_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
-            const T cnext = next_along_x<T, VW>(cx, cf, x0, i0, g.nx, lane);
-            const T unext = next_along_x<T, VW>(ulo, ud, x0, i0, g.nx, lane);
+        const bool row_start = i0 == 0, row_end = i0 + VW == g.nx;
+        const bool need_prev = lane == 0 || row_start, need_next = lane == 31 || row_end;
+        const int xp = row_start ? x0 + g.nx - 1 : x0 - 1;
+        const int xn = row_end ? x0 + VW - g.nx : x0 + VW;
+        // offset from the lane's first cell to the high neighbour along d of
+        // cell e (periodic)
+        auto hi_off = [&](int e) { return DX ? (e < VW - 1 ? e + 1 : xn - x0) : e + hi_d; };
+        // velocities of the chunk: signs, s = u dt / h, and the faces of the
+        // next sweep that an interfacial cell lists
+        T s_lo[VW], s_hi[VW];
+        uint32_t lo_nz = 0, lo_pos = 0, hi_nz = 0, hi_neg = 0, nf_lo = 0, nf_hi = 0;
+        {
+            const T* __restrict__ ud = B.u + (size_t)d * g.N;
+            const T* __restrict__ udn = B.u + (size_t)dn * g.N;
+            T ulo[VW], uhi[VW], unl[VW], unh[VW];
+            ld16(ud + x0, ulo);
+            ld16(udn + x0, unl);
+            if (DX) {
+                const T unext = next_along_x<T, VW>(ulo, ud, x0, i0, g.nx, lane);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) uhi[e] = e == VW - 1 ? unext : ulo[e + 1];
+            } else {
+                ld16(ud + x0 + hi_d, uhi);
+            }
+            if (dn == 0) {
+                const T nnext = next_along_x<T, VW>(unl, udn, x0, i0, g.nx, lane);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) unh[e] = e == VW - 1 ? nnext : unl[e + 1];
+            } else {
+                const int hi_dn = dn == 1 ? ic.hi_y : ic.hi_z;
+                ld16(udn + x0 + hi_dn, unh);
+            }
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                cl[e] = e == 0 ? cprev : cx[e - 1];
-                ch[e] = e == VW - 1 ? cnext : cx[e + 1];
-                uhi[e] = e == VW - 1 ? unext : ulo[e + 1];
+                const int sl = vsign(ulo[e]), sh = vsign(uhi[e]);
+                s_lo[e] = mul_rn(ulo[e], B.sfac);
+                s_hi[e] = mul_rn(uhi[e], B.sfac);
+                lo_nz |= (sl != 0 ? 1u : 0u) << e;
+                lo_pos |= (sl > 0 ? 1u : 0u) << e;
+                hi_nz |= (sh != 0 ? 1u : 0u) << e;
+                hi_neg |= (sh < 0 ? 1u : 0u) << e;
+                nf_lo |= (ic.valid && vsign(unl[e]) < 0 ? 1u : 0u) << e;
+                nf_hi |= (ic.valid && vsign(unh[e]) > 0 ? 1u : 0u) << e;
             }
-            xh_last = i0 + VW == g.nx ? VW - g.nx : VW;
-        } else {
-            ld16(cf + x0 + lo_d, cl);
-            ld16(cf + x0 + hi_d, ch);
-            ld16(ud + x0 + hi_d, uhi);
-        }
-        if (dn == 0) {
-            const T nnext = next_along_x<T, VW>(unl, udn, x0, i0, g.nx, lane);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) unh[e] = e == VW - 1 ? nnext : unl[e + 1];
-        } else {
-            ld16(udn + x0 + hi_dn, unh);
         }
         const size_t wpf = (size_t)g.rows * g.W;
-        const size_t word = (size_t)f * wpf + (size_t)ic.row * g.W + (i0 >> 5);
-        const int sh_bits = (lane * VW) & 31;
+        const size_t word0 = (size_t)ic.row * g.W + (i0 >> 5);
         const bool leader = ic.valid && (lane & (32 / VW - 1)) == 0;
-        uint32_t ccm = 0;
-        if (PH == 0) {
-            if (ic.valid) {
+        const T* __restrict__ cin = sweep_in(B, PH);
+        T* __restrict__ cout = sweep_out(B, PH);
+        FieldRow<T> cur, nxt;
+        load_field_row<T, PH, DX>(cur, cin, x0, lo_d, hi_d, need_prev, xp, need_next, xn, B.ccbits + word0);
+        for (int f = 0; f < B.K; ++f) {
+            if (f + 1 < B.K) {
+                const size_t nb = (size_t)(f + 1) * g.N;
+                load_field_row<T, PH, DX>(nxt, cin + nb, x0, lo_d, hi_d, need_prev, xp, need_next, xn,
+                                      B.ccbits + (size_t)(f + 1) * wpf + word0);
+            }
+            const size_t base = (size_t)f * g.N;
+            const size_t word = (size_t)f * wpf + word0;
+            if (DX) {
+                T cprev = __shfl_up_sync(0xffffffffu, cur.cx[VW - 1], 1);
+                T cnext = __shfl_down_sync(0xffffffffu, cur.cx[0], 1);
+                if (need_prev) cprev = cur.pv;
+                if (need_next) cnext = cur.nv;
 #pragma unroll
-                for (int e = 0; e < VW; ++e) ccm |= (above_half(cx[e]) ? 1u : 0u) << e;
-            }
-            const uint32_t w = gather_word<VW>(ccm, lane);
-            if (leader) B.ccbits[word] = w;
-        } else {
-            ccm = (B.ccbits[word] >> sh_bits) & ((1u << VW) - 1u);
-        }
-        T v[VW], rem[VW];
-        uint32_t occm = 0, flo = 0, fhi = 0;
-        bool clipped = false;
-        int nflag = 0;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            const int sl = vsign(ulo[e]), sh = vsign(uhi[e]);
-            const int kl = sl == 0 ? 0 : vclass(sl > 0 ? cl[e] : cx[e]);
-            const int kh = sh == 0 ? 0 : vclass(sh < 0 ? ch[e] : cx[e]);
-            const bool cc = (ccm >> e) & 1u;
-            const T s_lo = ulo[e] * B.sfac, s_hi = uhi[e] * B.sfac;
-            T F_lo = kl == 2 ? s_lo : T(0), F_hi = kh == 2 ? s_hi : T(0);
-            if (kl == 1) F_lo = flux[x0 + e];
-            if (kh == 1) F_hi = flux[x0 + (d == 0 ? (e < VW - 1 ? e + 1 : xh_last) : e + hi_d)];
-            // a cell that nothing enters or leaves keeps its bits (signed zero)
-            T ve = (kl | kh) == 0 && !cc ? cx[e] : cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi - s_lo);
-            rem[e] = T(0);
-            if (PH == 2) {
-                const bool clip = ve < T(0) || ve > T(1);
-                const T cl0 = ve < T(0) ? T(0) : T(1);
-                // ve - cl0 is exact (Sterbenz), so the FP64 sum below sees
-                // the same terms as a sum of FP64 differences
-                rem[e] = clip && ic.valid ? ve - cl0 : T(0);
-                clipped |= clip && ic.valid;
-                ve = clip ? cl0 : ve;
-                if (ic.valid && ve > tau) occm |= 1u << e;
-            }
-            v[e] = ve;
-            const bool interf = ic.valid && vclass(ve) == 1;
-            if (interf && vsign(unl[e]) < 0) {
-                flo |= 1u << e;
-                ++nflag;
-            }
-            if (interf && vsign(unh[e]) > 0) {
-                fhi |= 1u << e;
-                ++nflag;
-            }
-        }
-        if (ic.valid) st16(co + x0, v);
-        if (PH == 2) {
-            const uint32_t w = gather_word<VW>(occm, lane);
-            if (leader) B.occbits[word] = w;
-            if (__any_sync(0xffffffffu, clipped)) {
-                double removed = 0.0;
-#pragma unroll
-                for (int e = 0; e < VW; ++e) removed += (double)rem[e];
-                for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
-                if (lane == 0 && removed != 0.0) atomicAdd(B.clipped + f, removed);
-            }
-        }
-        int pos = warp_reserve(nflag, lane, &s_count);
-        if (nflag) {
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const int i = i0 + e;
-                if ((flo >> e) & 1u) seg[pos++] = box_face_key(bx, f, i, ic.j, ic.k);
-                if ((fhi >> e) & 1u) {
-                    int ih = i, jh = ic.j, kh2 = ic.k;
-                    if (dn == 0) ih = i + 1 == g.nx ? 0 : i + 1;
-                    else if (dn == 1) jh = ic.j + 1 == g.ny ? 0 : ic.j + 1;
-                    else kh2 = ic.k + 1 == g.nz ? 0 : ic.k + 1;
-                    seg[pos++] = box_face_key(bx, f, ih, jh, kh2);
+                for (int e = 0; e < VW; ++e) {
+                    cur.cl[e] = e == 0 ? cprev : cur.cx[e - 1];
+                    cur.ch[e] = e == VW - 1 ? cnext : cur.cx[e + 1];
                 }
             }
+            uint32_t ccm = 0;
+            if (PH == 0) {
+                if (ic.valid) {
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) ccm |= (above_half(cur.cx[e]) ? 1u : 0u) << e;
+                }
+                const uint32_t w = gather_word<VW>(ccm, lane);
+                if (leader) B.ccbits[word] = w;
+            } else {
+                ccm = (cur.ccw >> sh_bits) & ((1u << VW) - 1u);
+            }
+            // A warp whose cells and both neighbours along d are all empty
+            // (class 0) and carry no c_c bit has no flux through any face:
+            // every cell keeps its value and none is interfacial.
+            bool quiet = ccm == 0 || !ic.valid;
+#pragma unroll
+            for (int e = 0; e < VW; ++e)
+                quiet &= !ic.valid || (vclass(cur.cl[e]) | vclass(cur.cx[e]) | vclass(cur.ch[e])) == 0;
+            T v[VW];
+            uint32_t flo = 0, fhi = 0;
+            int nflag = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) v[e] = cur.cx[e];
+            if (!__all_sync(0xffffffffu, quiet)) {
+                const T* __restrict__ flux = B.flux + base;
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int kl = (lo_nz >> e) & 1u ? vclass((lo_pos >> e) & 1u ? cur.cl[e] : cur.cx[e]) : 0;
+                    const int kh = (hi_nz >> e) & 1u ? vclass((hi_neg >> e) & 1u ? cur.ch[e] : cur.cx[e]) : 0;
+                    const bool cc = (ccm >> e) & 1u;
+                    T F_lo = kl == 2 ? s_lo[e] : T(0), F_hi = kh == 2 ? s_hi[e] : T(0);
+                    if (kl == 1) F_lo = flux[x0 + e];
+                    if (kh == 1) F_hi = flux[x0 + hi_off(e)];
+                    // a cell that nothing enters or leaves keeps its bits (signed zero)
+                    if ((kl | kh) != 0 || cc)
+                        v[e] = cur.cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi[e] - s_lo[e]);
+                    if (PH == 2 && (v[e] < T(0) || v[e] > T(1))) continue;  // clipped below: not interfacial
+                    if (vclass(v[e]) == 1) {
+                        flo |= nf_lo & (1u << e);
+                        fhi |= nf_hi & (1u << e);
+                    }
+                }
+                nflag = __popc(flo) + __popc(fhi);
+            }
+            T rem[VW];
+            uint32_t occm = 0;
+            bool clipped = false;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                rem[e] = T(0);
+                if (PH == 2) {
+                    const bool clip = v[e] < T(0) || v[e] > T(1);
+                    const T cl0 = v[e] < T(0) ? T(0) : T(1);
+                    // v - cl0 is exact (Sterbenz), so the FP64 sum below sees
+                    // the same terms as a sum of FP64 differences
+                    rem[e] = clip && ic.valid ? v[e] - cl0 : T(0);
+                    clipped |= clip && ic.valid;
+                    v[e] = clip ? cl0 : v[e];
+                    if (ic.valid && v[e] > tau) occm |= 1u << e;
+                }
+            }
+            if (ic.valid) st16(cout + base + x0, v);
+            if (PH == 2) {
+                const uint32_t w = gather_word<VW>(occm, lane);
+                if (leader) B.occbits[word] = w;
+                if (__any_sync(0xffffffffu, clipped)) {
+                    double removed = 0.0;
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) removed += (double)rem[e];
+                    for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+                    if (lane == 0 && removed != 0.0) atomicAdd(B.clipped + f, removed);
+                }
+            }
+            if (__any_sync(0xffffffffu, nflag != 0)) {
+                int pos = warp_reserve(nflag, lane, &s_count);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int i = i0 + e;
+                    if ((flo >> e) & 1u) seg[pos++] = box_face_key(bx, f, i, ic.j, ic.k);
+                    if ((fhi >> e) & 1u) {
+                        int ih = i, jh = ic.j, kh2 = ic.k;
+                        if (dn == 0) ih = i + 1 == g.nx ? 0 : i + 1;
+                        else if (dn == 1) jh = ic.j + 1 == g.ny ? 0 : ic.j + 1;
+                        else kh2 = ic.k + 1 == g.nz ? 0 : ic.k + 1;
+                        seg[pos++] = box_face_key(bx, f, ih, jh, kh2);
+                    }
+                }
+            }
+            cur = nxt;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) ncounts[blockIdx.x] = s_count;
 }
 
-// Launch of the update pass of sweep `sweep` (0, 1, 2).
+// Launch of the update pass of sweep `sweep` (0, 1, 2) along d.
+template <typename T, int NB, int PH>
+inline void launch_update_ph(const BoxSet<T, NB>& S, int d, int dn, T tau, unsigned long long* nlist, long long cap,
+                             int* ncounts, int gb, int threads, cudaStream_t st) {
+    if (d == 0)
+        k_update_bx<T, NB, PH, true><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+    else
+        k_update_bx<T, NB, PH, false><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+}
 template <typename T, int NB>
 inline void launch_update_bx(const BoxSet<T, NB>& S, int d, int dn, int sweep, T tau, unsigned long long* nlist,
                              long long cap, int* ncounts, int gb, int threads, cudaStream_t st) {
     if (sweep == 0)
-        k_update_bx<T, NB, 0><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+        launch_update_ph<T, NB, 0>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
     else if (sweep == 1)
-        k_update_bx<T, NB, 1><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+        launch_update_ph<T, NB, 1>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
     else
-        k_update_bx<T, NB, 2><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+        launch_update_ph<T, NB, 2>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
 }
 
 // A listed face of a box set: box, field, the cell x of the face's high

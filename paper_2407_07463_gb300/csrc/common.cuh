@@ -27,6 +27,11 @@ __host__ __device__ inline Dims make_dims(int nx, int ny, int nz) {
     return d;
 }
 
+// Product rounded on its own, never fused into a neighbouring add, so that
+// every instantiation of a kernel rounds it the same way.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;

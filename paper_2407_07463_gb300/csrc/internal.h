@@ -93,7 +93,7 @@ inline long long list_reserve(int nx, int ny, int nz, int K, int es) {
     const long long rows = (long long)ny * nz, words = rows * ((nx + 31) / 32);
     const long long scalar = 2LL * 32 * K * (words + kSweepBlocks);
     const long long CH = 512 / es, cpr = (nx + CH - 1) / CH;
-    const long long vec = 2LL * CH * ((long long)K * rows * cpr + 8LL * kListBlocks);
+    const long long vec = 2LL * CH * K * (rows * cpr + 8LL * kListBlocks);
     return scalar > vec ? scalar : vec;
 }
 
