@@ -4,6 +4,7 @@
 #pragma once
 
 #include <math.h>
+#include <stdint.h>
 
 #include "plic.cuh"
 
@@ -30,13 +31,15 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 template <int STRIDE>
 static __device__ __noinline__ float normal_residual_m(const float* st, const float m[3], float* alpha) {
     const float m0 = m[0], m1 = m[1], m2 = m[2];
-    const float al = plic_alpha<float>(m0, m1, m2, st[13 * STRIDE]);
-    *alpha = al;
     // x_i -> 1 - x_i for a negative component moves the constant by |m_i|
     const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
     sort3(a, b, c);
     const VolRecip r = vol_recip(a, b, c);
+    // the plane constant in the reflected frame, and in the grid's
+    const float A = alpha_r(r, st[13 * STRIDE]);
+    const float al = A - off;
+    *alpha = al;
     // first pass: the cells the plane leaves whole (volume 0 or 1) cost a
     // compare; the cut ones are collected in a mask and take the volume in a
     // second pass (about a third of the 27 for a plane through the centre)
@@ -45,7 +48,7 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float aq = al + off - (m0 * i + m1 * j + m2 * k);
+        const float aq = A - (m0 * i + m1 * j + m2 * k);
         if (aq > 0.f && aq < r.S)
             cut |= 1u << q;
         else
@@ -55,7 +58,7 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
         const int q = __ffs(cut) - 1;
         cut &= cut - 1u;
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float v = vol_fast_r(r, al + off - (m0 * i + m1 * j + m2 * k));
+        const float v = vol_fast_r(r, A - (m0 * i + m1 * j + m2 * k));
         e += fabsf(v - st[q * STRIDE]);
     }
     return e * (1.f / 27.f);

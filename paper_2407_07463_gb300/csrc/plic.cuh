@@ -387,6 +387,87 @@ __device__ __forceinline__ double plic_alpha_banded(double m0, double m1, double
     return plic_alpha<double>(m0, m1, m2, cv);
 }
 
+// FP32 plane constant for a normal whose reciprocals are already taken (the
+// judge evaluates many volumes per normal): the regions and roots of
+// alpha_sorted, with products by the reciprocals in place of divisions and
+// the polish on vol_fast_r and its derivative.
+__device__ __forceinline__ float vdf1r(float x, float a, float ia) {
+    return x >= a ? 2.f * x - a : (x > 0.f ? x * x * ia : 0.f);
+}
+__device__ __forceinline__ float vdf2r(float x, const VolRecip& r) {
+    const float dir = (vdf1r(x, r.a, r.ia) - vdf1r(x - r.b, r.a, r.ia)) * r.ib;
+    const float der = x >= r.a ? 2.f : (x > 0.f ? 2.f * x * r.ia : 0.f);
+    return r.b0 ? der : (x - r.b >= r.a ? 2.f : dir);
+}
+__device__ __forceinline__ float dvol_fast_r(const VolRecip& r, float alpha) {
+    const float x = 2.f * alpha > r.S ? r.S - alpha : alpha;
+    const float d = (vdf2r(x, r) - vdf2r(x - r.c, r)) * (3.f * r.i6c);  // 1/(2c) = 3/(6c)
+    return alpha <= 0.f || alpha >= r.S ? 0.f : d;
+}
+// Root in (0, S/2] of the volume = v, 0 < v <= 1/2.
+static __device__ __noinline__ float alpha_sorted_r(const VolRecip& r, float v) {
+    const float a = r.a, b = r.b, c = r.c;
+    if (a <= PlicConst<float>::tiny) {
+        if (b <= PlicConst<float>::tiny) return c * v;
+        const float t = sqrtf(2.f * b * c * v);
+        return t < b ? t : c * v + 0.5f * b;
+    }
+    const float i6bc = r.ib * r.i6c;  // 1/(6bc)
+    float al;
+    if (v <= a * a * i6bc) {
+        al = cbrtf(6.f * a * b * c * v);
+    } else if (v <= (b * b - a * b + a * a * (1.f / 3.f)) * (3.f * i6bc)) {
+        const float disc = 8.f * b * c * v - a * a * (1.f / 3.f);
+        al = 0.5f * (a + sqrtf(fmaxf(disc, 0.f)));
+    } else {
+        const float ab = a + b;
+        const bool prism = c >= ab;
+        float hi;
+        if (prism && v >= ab * (3.f * r.i6c)) {
+            al = c * v + 0.5f * ab;
+            hi = -1.f;
+        } else {
+            hi = prism ? ab : 0.5f * r.S;
+        }
+        if (hi > 0.f) {
+            const float rhs = 6.f * a * b * c * v;
+            al = hi;
+            for (int it = 0; it < PlicConst<float>::newton_iters; ++it) {
+                const float da = al - a, db = al - b, dc = al - c;
+                float f = al * al * al - da * da * da - db * db * db - rhs;
+                float fp = al * al - da * da - db * db;
+                if (dc > 0.f) {
+                    f -= dc * dc * dc;
+                    fp -= dc * dc;
+                }
+                fp *= 3.f;
+                if (!(fp > 0.f)) break;
+                const float stp = __fdividef(f, fp);
+                al -= stp;
+                if (al < b) {
+                    al = b;
+                    break;
+                }
+                if (fabsf(stp) <= PlicConst<float>::newton_rtol * al) break;
+            }
+        }
+    }
+    const float dv = dvol_fast_r(r, al);
+    if (dv > 0.f) {
+        const float nal = al - __fdividef(vol_fast_r(r, al) - v, dv);
+        if (nal > 0.f && nal <= 0.5f * r.S) al = nal;
+    }
+    return al;
+}
+// Plane constant in the reflected, sorted frame for fraction cv.
+__device__ __forceinline__ float alpha_r(const VolRecip& r, float cv) {
+    if (cv <= 0.f) return 0.f;
+    if (cv >= 1.f) return r.S;
+    const bool flip = cv > 0.5f;
+    const float al = alpha_sorted_r(r, flip ? 1.f - cv : cv);
+    return flip ? r.S - al : al;
+}
+
 // ---------------------------------------------------------------------------
 // Normals.  Stencil st[(k+1)*9 + (j+1)*3 + (i+1)], offsets i (x), j (y), k (z).
 
