@@ -24,10 +24,10 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 // holding the centre cell's volume fraction, extended over the 3x3x3 block;
 // the mean over the 27 cells of |predicted - actual| fraction.  *alpha gets
 // that plane's constant (FP32).  The reflection and ordering of the normal
-// are done once per stencil (with the reciprocals the volume needs) and
-// every cell takes the branch-free volume (vol_fast_r), so all lanes of a
-// warp run the same instructions.  The value
-// of cell q is st[q * STRIDE] (STRIDE > 1: a column of a shared-memory tile).
+// and the constants of its volume are taken once per stencil; the cells
+// the plane leaves whole cost a compare, the cut ones the piecewise closed
+// form (vol_pw).  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
+// column of a shared-memory tile).
 template <int STRIDE>
 static __device__ __noinline__ float normal_residual_m(const float* st, const float m[3], float* alpha) {
     const float m0 = m[0], m1 = m[1], m2 = m[2];
@@ -35,11 +35,10 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
     const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
     sort3(a, b, c);
-    const VolRecip r = vol_recip(a, b, c);
+    const VolPW p = vol_pw_make(a, b, c);
     // the plane constant in the reflected frame, and in the grid's
-    const float A = alpha_r(r, st[13 * STRIDE]);
-    const float al = A - off;
-    *alpha = al;
+    const float A = alpha_pw(p, st[13 * STRIDE]);
+    *alpha = A - off;
     // first pass: the cells the plane leaves whole (volume 0 or 1) cost a
     // compare; the cut ones are collected in a mask and take the volume in a
     // second pass (about a third of the 27 for a plane through the centre)
@@ -49,7 +48,7 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
     for (int q = 0; q < 27; ++q) {
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
         const float aq = A - (m0 * i + m1 * j + m2 * k);
-        if (aq > 0.f && aq < r.S)
+        if (aq > 0.f && aq < p.S)
             cut |= 1u << q;
         else
             e += fabsf((aq <= 0.f ? 0.f : 1.f) - st[q * STRIDE]);
@@ -58,7 +57,7 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
         const int q = __ffs(cut) - 1;
         cut &= cut - 1u;
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float v = vol_fast_r(r, A - (m0 * i + m1 * j + m2 * k));
+        const float v = vol_pw(p, A - (m0 * i + m1 * j + m2 * k));
         e += fabsf(v - st[q * STRIDE]);
     }
     return e * (1.f / 27.f);

@@ -129,95 +129,140 @@ __device__ __forceinline__ void sort3(T& a, T& b, T& c) {
     if (a > b) { t = a; a = b; b = t; }
 }
 
-// Branch-free FP32 volume for sorted 0 <= a <= b <= c (c > 0), S = a+b+c,
-// any alpha.  The inclusion-exclusion closed form
-//   V = sum over the 8 vertex sums s of (-1)^|s| (alpha - s)_+^3 / (6abc)
-// is rewritten as nested divided differences of P(x) = x_+^3,
-//   V = [H(alpha) - H(alpha - c)] / (6c),  H(x) = [D(x) - D(x - b)] / b,
-//   D(x) = [P(x) - P(x - a)] / a,
-// each taken in the form that has no cancellation: D(x) = 3x^2 - 3xa + a^2
-// when x >= a (else x^3 / a, or 0), H(x) = 3(2x - b - a) when x - b >= a
-// (else the plain difference, whose terms are then O(b^2)), and the
-// derivatives of D in the limit b -> 0.  With V(alpha) = 1 - V(S - alpha)
-// for alpha > S/2 the result is within a few ulp of the exact volume for
-// every normal, including a = 0 and a = b = 0 (no division by a small
-// product, unlike the closed form itself).
-__device__ __forceinline__ float vdd1(float x, float a) {
-    const float p = 3.f * x * x - 3.f * x * a + a * a;
-    const float q = x > 0.f ? x * x * x / a : 0.f;
-    return x >= a ? p : q;
-}
-__device__ __forceinline__ float vdd1_d(float x, float a) {
-    return x >= a ? 6.f * x - 3.f * a : (x > 0.f ? 3.f * x * x / a : 0.f);
-}
-__device__ __forceinline__ float vdd2(float x, float a, float b) {
-    const float lin = 3.f * (2.f * x - b - a);
-    const float dir = (vdd1(x, a) - vdd1(x - b, a)) / b;
-    return b <= 1e-30f ? vdd1_d(x, a) : (x - b >= a ? lin : dir);
-}
-__device__ __forceinline__ float vol_fast(float a, float b, float c, float S, float alpha) {
-    const bool flip = 2.f * alpha > S;
-    const float x = flip ? S - alpha : alpha;
-    const float v = (vdd2(x, a, b) - vdd2(x - c, a, b)) / (6.f * c);
-    const float r = flip ? 1.f - v : v;
-    return alpha <= 0.f ? 0.f : (alpha >= S ? 1.f : r);
-}
-
-// d vol_fast / d alpha (the cut area of the plane in the cube), by the same
-// nested divided differences one order lower: with E(x) = x_+^2,
-//   dV/dalpha = [G(alpha) - G(alpha - c)] / (2c),  G(x) = [F(x) - F(x - b)] / b,
-//   F(x) = [E(x) - E(x - a)] / a = 2x - a (x >= a), x^2 / a (0 < x < a), 0.
-__device__ __forceinline__ float vdf1(float x, float a) {
-    return x >= a ? 2.f * x - a : (x > 0.f ? x * x / a : 0.f);
-}
-__device__ __forceinline__ float vdf2(float x, float a, float b) {
-    const float lin = 2.f;
-    const float dir = (vdf1(x, a) - vdf1(x - b, a)) / b;
-    const float der = x >= a ? 2.f : (x > 0.f ? 2.f * x / a : 0.f);
-    return b <= 1e-30f ? der : (x - b >= a ? lin : dir);
-}
-__device__ __forceinline__ float dvol_fast(float a, float b, float c, float S, float alpha) {
-    if (alpha <= 0.f || alpha >= S) return 0.f;
-    const float x = 2.f * alpha > S ? S - alpha : alpha;  // the area is symmetric
-    return (vdf2(x, a, b) - vdf2(x - c, a, b)) / (2.f * c);
-}
-
-// The same with the reciprocals of one normal taken once (many plane
-// constants per normal): ia = 1/a, ib = 1/b, i6c = 1/(6c); a product
-// replaces each division (results within a few ulp of vol_fast's).
-struct VolRecip {
-    float a, b, c, S, ia, ib, i6c;
-    bool b0;  // b <= 1e-30: the b -> 0 limit
+// FP32 volume, piecewise closed form.  For sorted 0 <= a <= b <= c the
+// inclusion-exclusion formula of Scardovelli & Zaleski (2000, JCP 164)
+//   6abc V(x) = sum over the 8 vertex sums s of (-1)^|s| (x - s)_+^3
+// is taken on x = min(alpha, S - alpha) <= S/2 (V(alpha) = 1 - V(S - alpha)
+// above S/2).  There only the terms of s = 0, a, b, c, a + b can be active,
+// and pairing x^3 with (x - a)^3 and (x - b)^3 with (x - a - b)^3 leaves no
+// division of a large term by a small product:
+//   x <= a:                 V = x^3 / (6abc)
+//   x > a + b (when c >= a + b, the prism): V = (2x - a - b) / (2c)
+//   otherwise:              V = [3x(x - a) + a^2] / (6bc)
+//                               - [(x - b)_+^3 + (x - c)_+^3] / (6abc)
+// where (x - b)_+ <= a and (x - c)_+ <= a/2 on the last piece, so its
+// correction is O(a^2 / bc).  The constants of one normal are taken once
+// (many plane constants per normal in the judge); the normal is expected
+// L1-normalised (S = 1 up to rounding): plic_volume and plic_alpha scale any
+// other to it.  Where a (or b) is so small that 1/(6abc) (or the pieces it
+// bounds) fall below FP32 resolution, its limit is used: the x <= a piece
+// and the correction vanish (b -> 0: the prism's linear piece from x = 0).
+struct VolPW {
+    float a, b, c, S, ab;
+    float x_lin;  // the linear piece lies above it
+    float i6bc;   // 1/(6bc)
+    float i6abc;  // 1/(6abc), 0 in the limit a -> 0
+    float k_lin;  // 1/(2c)
 };
-__device__ __forceinline__ VolRecip vol_recip(float a, float b, float c) {
-    VolRecip r;
-    r.a = a;
-    r.b = b;
-    r.c = c;
-    r.S = a + b + c;
-    r.ia = 1.f / a;
-    r.ib = 1.f / b;
-    r.i6c = 1.f / (6.f * c);
-    r.b0 = b <= 1e-30f;
-    return r;
+__device__ __forceinline__ VolPW vol_pw_make(float a, float b, float c) {
+    VolPW p;
+    p.a = a;
+    p.b = b;
+    p.c = c;
+    p.S = a + b + c;
+    p.ab = a + b;
+    const bool b0 = b <= PlicConst<float>::tiny;
+    p.x_lin = b0 ? -1.f : (c >= p.ab ? p.ab : INFINITY);
+    p.i6bc = 1.f / (6.f * b * c);
+    const float i6abc = p.i6bc / a;
+    p.i6abc = (a > PlicConst<float>::tiny && !b0 && isfinite(i6abc)) ? i6abc : 0.f;
+    p.k_lin = 0.5f / c;
+    return p;
 }
-__device__ __forceinline__ float vdd1r(float x, float a, float ia) {
-    const float p = 3.f * x * x - 3.f * x * a + a * a;
-    const float q = x > 0.f ? x * x * x * ia : 0.f;
-    return x >= a ? p : q;
+__device__ __forceinline__ float vol_pw(const VolPW& p, float alpha) {
+    const bool flip = 2.f * alpha > p.S;
+    const float x = flip ? p.S - alpha : alpha;
+    const float lin = (2.f * x - p.ab) * p.k_lin;
+    const float v1 = x * x * x * p.i6abc;
+    const float tb = fmaxf(x - p.b, 0.f), tc = fmaxf(x - p.c, 0.f);
+    const float v3 = (3.f * x * (x - p.a) + p.a * p.a) * p.i6bc - (tb * tb * tb + tc * tc * tc) * p.i6abc;
+    const float v = x > p.x_lin ? lin : (x <= p.a ? v1 : v3);
+    const float r = flip ? 1.f - v : v;
+    return alpha <= 0.f ? 0.f : (alpha >= p.S ? 1.f : r);
 }
-__device__ __forceinline__ float vdd2r(float x, const VolRecip& r) {
-    const float lin = 3.f * (2.f * x - r.b - r.a);
-    const float dir = (vdd1r(x, r.a, r.ia) - vdd1r(x - r.b, r.a, r.ia)) * r.ib;
-    const float der = x >= r.a ? 6.f * x - 3.f * r.a : (x > 0.f ? 3.f * x * x * r.ia : 0.f);
-    return r.b0 ? der : (x - r.b >= r.a ? lin : dir);
+// dV/dalpha (the cut area of the plane in the cube), piece by piece.
+__device__ __forceinline__ float dvol_pw(const VolPW& p, float alpha) {
+    const float x = 2.f * alpha > p.S ? p.S - alpha : alpha;  // the area is symmetric
+    const float tb = fmaxf(x - p.b, 0.f), tc = fmaxf(x - p.c, 0.f);
+    const float d1 = 3.f * x * x * p.i6abc;
+    const float d3 = (6.f * x - 3.f * p.a) * p.i6bc - 3.f * (tb * tb + tc * tc) * p.i6abc;
+    const float d = x > p.x_lin ? 2.f * p.k_lin : (x <= p.a ? d1 : d3);
+    return alpha <= 0.f || alpha >= p.S ? 0.f : d;
 }
-__device__ __forceinline__ float vol_fast_r(const VolRecip& r, float alpha) {
-    const bool flip = 2.f * alpha > r.S;
-    const float x = flip ? r.S - alpha : alpha;
-    const float v = (vdd2r(x, r) - vdd2r(x - r.c, r)) * r.i6c;
-    const float res = flip ? 1.f - v : v;
-    return alpha <= 0.f ? 0.f : (alpha >= r.S ? 1.f : res);
+
+// Root in (0, S/2] of vol_pw = v, 0 < v <= 1/2: the regions of alpha_sorted
+// below (closed forms in regions 1, 2 and the prism, Newton on the cubic in
+// 3 and 4), with products by the normal's constants in place of divisions,
+// then one Newton step on vol_pw.  *region as for alpha_sorted.
+static __device__ __noinline__ float alpha_sorted_pw(const VolPW& p, float v, int* region = nullptr) {
+    const float a = p.a, b = p.b, c = p.c;
+    if (a <= PlicConst<float>::tiny) {
+        // plane parallel to one axis: the 2D area function
+        if (region) *region = 0;
+        if (b <= PlicConst<float>::tiny) return c * v;
+        const float t = sqrtf(2.f * b * c * v);
+        return t < b ? t : c * v + 0.5f * b;
+    }
+    float al;
+    int reg;
+    if (v <= a * a * p.i6bc) {
+        al = cbrtf(6.f * a * b * c * v);
+        reg = 1;
+    } else if (v <= (b * b - a * b + a * a * (1.f / 3.f)) * (3.f * p.i6bc)) {
+        const float disc = 8.f * b * c * v - a * a * (1.f / 3.f);
+        al = 0.5f * (a + sqrtf(fmaxf(disc, 0.f)));
+        reg = 2;
+    } else {
+        const bool prism = c >= p.ab;
+        float hi;
+        if (prism && v >= p.ab * p.k_lin) {
+            al = c * v + 0.5f * p.ab;
+            hi = -1.f;
+            reg = 5;
+        } else {
+            hi = prism ? p.ab : 0.5f * p.S;
+            reg = 3;
+        }
+        if (hi > 0.f) {
+            // Newton on 6abc V = al^3 - (al-a)^3 - (al-b)^3 - [(al-c)^3]
+            const float rhs = 6.f * a * b * c * v;
+            al = hi;
+            for (int it = 0; it < PlicConst<float>::newton_iters; ++it) {
+                const float da = al - a, db = al - b, dc = al - c;
+                float f = al * al * al - da * da * da - db * db * db - rhs;
+                float fp = al * al - da * da - db * db;
+                if (dc > 0.f) {
+                    f -= dc * dc * dc;
+                    fp -= dc * dc;
+                }
+                fp *= 3.f;
+                if (!(fp > 0.f)) break;
+                const float stp = __fdividef(f, fp);
+                al -= stp;
+                if (al < b) {
+                    al = b;
+                    break;
+                }
+                if (fabsf(stp) <= PlicConst<float>::newton_rtol * al) break;
+            }
+            if (al > c) reg = 4;
+        }
+    }
+    const float dv = dvol_pw(p, al);
+    if (dv > 0.f) {
+        const float nal = al - __fdividef(vol_pw(p, al) - v, dv);
+        if (nal > 0.f && nal <= 0.5f * p.S) al = nal;
+    }
+    if (region) *region = reg;
+    return al;
+}
+// Plane constant in the reflected, sorted frame for fraction cv.
+__device__ __forceinline__ float alpha_pw(const VolPW& p, float cv) {
+    if (cv <= 0.f) return 0.f;
+    if (cv >= 1.f) return p.S;
+    const bool flip = cv > 0.5f;
+    const float al = alpha_sorted_pw(p, flip ? 1.f - cv : cv);
+    return flip ? p.S - al : al;
 }
 
 // Volume of {x in [0,1]^3 : m.x < alpha}.
@@ -229,16 +274,20 @@ __device__ __noinline__ T plic_volume(T m0, T m1, T m2, T alpha) {
     sort3(m0, m1, m2);
     T S = m0 + m1 + m2;
     if (S <= T(0)) return alpha > T(0) ? T(1) : T(0);
-    if constexpr (std::is_same<T, float>::value) return vol_fast(m0, m1, m2, S, alpha);
+    if constexpr (std::is_same<T, float>::value) {
+        const float is = 1.f / S;
+        return vol_pw(vol_pw_make(m0 * is, m1 * is, m2 * is), alpha * is);
+    }
     if (alpha <= T(0)) return T(0);
     if (alpha >= S) return T(1);
     if (T(2) * alpha > S) return T(1) - vol_sorted(m0, m1, m2, S - alpha);
     return vol_sorted(m0, m1, m2, alpha);
 }
 
-// Root alpha in (0, S/2] of vol_sorted(a,b,c,alpha) = v, 0 < v <= 1/2.
-// *region (if not null) receives the piece the root lies in: 0 for the 2D
-// cases (a = 0), 1..4 the cubic regions, 5 the prism region.
+// Root alpha in (0, S/2] of vol_sorted(a,b,c,alpha) = v, 0 < v <= 1/2
+// (FP64; FP32 roots come from alpha_sorted_pw).  *region (if not null)
+// receives the piece the root lies in: 0 for the 2D cases (a = 0), 1..4 the
+// cubic regions, 5 the prism region.
 template <typename T>
 __device__ __noinline__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr) {
     T al;
@@ -298,16 +347,10 @@ __device__ __noinline__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr
             }
         }
     }
-    // polish on the exact piecewise form (FP32: its branch-free evaluation)
-    T S = a + b + c;
-    T dv, vv;
-    if constexpr (std::is_same<T, float>::value) {
-        dv = dvol_fast(a, b, c, S, al);
-        vv = vol_fast(a, b, c, S, al);
-    } else {
-        dv = dvol_sorted(a, b, c, al);
-        vv = dv > T(0) ? vol_sorted(a, b, c, al) : T(0);
-    }
+    // polish on the exact piecewise form
+    const T S = a + b + c;
+    const T dv = dvol_sorted(a, b, c, al);
+    const T vv = dv > T(0) ? vol_sorted(a, b, c, al) : T(0);
     if (dv > T(0)) {
         T nal = al - (vv - v) / dv;
         if (nal > T(0) && nal <= T(0.5) * S) al = nal;
@@ -355,7 +398,13 @@ __device__ __noinline__ T plic_alpha(T m0, T m1, T m2, T cv) {
     if (cv >= T(1)) return off + S;
     bool flip = cv > T(0.5);
     T v = flip ? T(1) - cv : cv;
-    T al = alpha_sorted(m0, m1, m2, v);
+    T al;
+    if constexpr (std::is_same<T, float>::value) {
+        const float is = 1.f / S;
+        al = S * alpha_sorted_pw(vol_pw_make(m0 * is, m1 * is, m2 * is), v);
+    } else {
+        al = alpha_sorted(m0, m1, m2, v);
+    }
     if (flip) al = S - al;
     return al + off;
 }
@@ -377,7 +426,8 @@ __device__ __forceinline__ float plic_alpha_banded(float m0, float m1, float m2,
     bool flip = cv > 0.5f;
     double v = flip ? 1.0 - (double)cv : (double)cv;
     int reg = 0;
-    float al32 = alpha_sorted<float>(m0, m1, m2, (float)v, &reg);
+    const float is = 1.f / S;
+    const float al32 = S * alpha_sorted_pw(vol_pw_make(m0 * is, m1 * is, m2 * is), (float)v, &reg);
     double al = alpha_refine_fp64((double)m0, (double)m1, (double)m2, v, (double)al32, reg);
     if (flip) al = (double)S - al;
     return (float)(al + (double)off);
@@ -385,87 +435,6 @@ __device__ __forceinline__ float plic_alpha_banded(float m0, float m1, float m2,
 __device__ __forceinline__ double plic_alpha_banded(double m0, double m1, double m2, double cv,
                                                     double) {
     return plic_alpha<double>(m0, m1, m2, cv);
-}
-
-// FP32 plane constant for a normal whose reciprocals are already taken (the
-// judge evaluates many volumes per normal): the regions and roots of
-// alpha_sorted, with products by the reciprocals in place of divisions and
-// the polish on vol_fast_r and its derivative.
-__device__ __forceinline__ float vdf1r(float x, float a, float ia) {
-    return x >= a ? 2.f * x - a : (x > 0.f ? x * x * ia : 0.f);
-}
-__device__ __forceinline__ float vdf2r(float x, const VolRecip& r) {
-    const float dir = (vdf1r(x, r.a, r.ia) - vdf1r(x - r.b, r.a, r.ia)) * r.ib;
-    const float der = x >= r.a ? 2.f : (x > 0.f ? 2.f * x * r.ia : 0.f);
-    return r.b0 ? der : (x - r.b >= r.a ? 2.f : dir);
-}
-__device__ __forceinline__ float dvol_fast_r(const VolRecip& r, float alpha) {
-    const float x = 2.f * alpha > r.S ? r.S - alpha : alpha;
-    const float d = (vdf2r(x, r) - vdf2r(x - r.c, r)) * (3.f * r.i6c);  // 1/(2c) = 3/(6c)
-    return alpha <= 0.f || alpha >= r.S ? 0.f : d;
-}
-// Root in (0, S/2] of the volume = v, 0 < v <= 1/2.
-static __device__ __noinline__ float alpha_sorted_r(const VolRecip& r, float v) {
-    const float a = r.a, b = r.b, c = r.c;
-    if (a <= PlicConst<float>::tiny) {
-        if (b <= PlicConst<float>::tiny) return c * v;
-        const float t = sqrtf(2.f * b * c * v);
-        return t < b ? t : c * v + 0.5f * b;
-    }
-    const float i6bc = r.ib * r.i6c;  // 1/(6bc)
-    float al;
-    if (v <= a * a * i6bc) {
-        al = cbrtf(6.f * a * b * c * v);
-    } else if (v <= (b * b - a * b + a * a * (1.f / 3.f)) * (3.f * i6bc)) {
-        const float disc = 8.f * b * c * v - a * a * (1.f / 3.f);
-        al = 0.5f * (a + sqrtf(fmaxf(disc, 0.f)));
-    } else {
-        const float ab = a + b;
-        const bool prism = c >= ab;
-        float hi;
-        if (prism && v >= ab * (3.f * r.i6c)) {
-            al = c * v + 0.5f * ab;
-            hi = -1.f;
-        } else {
-            hi = prism ? ab : 0.5f * r.S;
-        }
-        if (hi > 0.f) {
-            const float rhs = 6.f * a * b * c * v;
-            al = hi;
-            for (int it = 0; it < PlicConst<float>::newton_iters; ++it) {
-                const float da = al - a, db = al - b, dc = al - c;
-                float f = al * al * al - da * da * da - db * db * db - rhs;
-                float fp = al * al - da * da - db * db;
-                if (dc > 0.f) {
-                    f -= dc * dc * dc;
-                    fp -= dc * dc;
-                }
-                fp *= 3.f;
-                if (!(fp > 0.f)) break;
-                const float stp = __fdividef(f, fp);
-                al -= stp;
-                if (al < b) {
-                    al = b;
-                    break;
-                }
-                if (fabsf(stp) <= PlicConst<float>::newton_rtol * al) break;
-            }
-        }
-    }
-    const float dv = dvol_fast_r(r, al);
-    if (dv > 0.f) {
-        const float nal = al - __fdividef(vol_fast_r(r, al) - v, dv);
-        if (nal > 0.f && nal <= 0.5f * r.S) al = nal;
-    }
-    return al;
-}
-// Plane constant in the reflected, sorted frame for fraction cv.
-__device__ __forceinline__ float alpha_r(const VolRecip& r, float cv) {
-    if (cv <= 0.f) return 0.f;
-    if (cv >= 1.f) return r.S;
-    const bool flip = cv > 0.5f;
-    const float al = alpha_sorted_r(r, flip ? 1.f - cv : cv);
-    return flip ? r.S - al : al;
 }
 
 // ---------------------------------------------------------------------------
