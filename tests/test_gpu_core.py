@@ -103,6 +103,28 @@ def test_plic_alpha_mixed(vof):
     assert err.max() <= 2e-6
 
 
+def test_plic_volume_fp32(vof):
+    """FP32 volume (the piecewise closed form) against the oracle's volume of
+    the same float inputs: arbitrary planes, including ones that miss the
+    cube, normals with zero or tiny components, and unnormalised scales."""
+    rng = np.random.default_rng(4)
+    n = 20000
+    m = random_normals(rng, n)
+    k = rng.integers(0, 3, size=n)
+    tiny = rng.random(n) < 0.1
+    m[tiny, k[tiny]] *= 10.0 ** rng.uniform(-12, -3, tiny.sum())
+    scale = np.where(np.arange(n) < n // 2, 1.0, 10.0 ** rng.uniform(-6, 3, n))
+    m = (m * scale[:, None]).astype(np.float32)
+    m64 = m.astype(np.float64)
+    lo = np.minimum(m64, 0).sum(1)
+    al = (lo + rng.uniform(-0.05, 1.05, n) * np.abs(m64).sum(1)).astype(np.float32)
+    v = vof.vof_plic_volume(torch.from_numpy(m).to(DEV), torch.from_numpy(al).to(DEV), precision=1)
+    v = v.cpu().numpy().astype(np.float64)
+    vo = np.array([O.plic_volume(m64[t], float(al[t])) for t in range(n)])
+    err = np.abs(v - vo)
+    assert err.max() <= 1e-6, (err.max(), m[err.argmax()], al[err.argmax()])
+
+
 # ---------------------------------------------------------------- normals
 
 
