@@ -94,11 +94,12 @@ __device__ __forceinline__ void store_pairs8(unsigned char* tile, int r, int k0,
     uint32_t hi[4], lo[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        __nv_bfloat16 h0, l0, h1, l1;
-        split_bf16(v[2 * q], h0, l0);
-        split_bf16(v[2 * q + 1], h1, l1);
-        hi[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        lo[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        // split_bf16 on two values at once: one packed conversion per part
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+        hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[q] = *reinterpret_cast<const uint32_t*>(&l);
     }
     *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(r, k0, kext)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(r, k0 + half, kext)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);

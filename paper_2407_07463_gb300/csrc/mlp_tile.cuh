@@ -122,15 +122,15 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     tc::fence_after_sync();
     if (t == 0) issue_layer(taddr + kColD2, s.H, kHidHL, s.W2, kHid, kHid, &s.bar);
     if (!finish_layer(s, phase)) return false;
-    float h2[kHid];
+    // layer 2 has finished reading H: its output goes there as layer 3's input
     for (int c0 = 0; c0 < kHid; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + lane_off + kColD2 + c0, v);
-        for (int q = 0; q < 16; ++q) h2[c0 + q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
-    }
-    // layer 2 has finished reading H: reuse it for layer 3's input
 #pragma unroll
-    for (int k0 = 0; k0 < kHid; k0 += 8) store_pairs8(s.H, t, k0, kHid, kHidHL, h2 + k0);
+        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
+        store_pairs8(s.H, t, c0, kHid, kHidHL, v);
+        store_pairs8(s.H, t, c0 + 8, kHid, kHidHL, v + 8);
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
