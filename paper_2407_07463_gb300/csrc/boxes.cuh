@@ -464,6 +464,7 @@ inline void launch_update_bx(const BoxSet<T, NB>& S, int d, int dn, int sweep, T
 // side, the flux index t = f N + x, the upwind donor.
 struct BoxFace {
     int box, f, x, donor;
+    int di, dj, dk;  // the donor's cell coordinates
     size_t t;
 };
 
@@ -479,7 +480,16 @@ __device__ __forceinline__ BoxFace decode_box_face(const BoxSet<T, NB>& S, unsig
     r.x = cell(i, j, k, g);
     r.t = (size_t)r.f * g.N + r.x;
     uv = S.b[r.box].u[(size_t)d * g.N + r.x];
-    r.donor = vsign(uv) > 0 ? step_cell(r.x, i, j, k, d, -1, g) : r.x;
+    // upwind donor: the face's cell, or its low neighbour along d (periodic)
+    r.di = i;
+    r.dj = j;
+    r.dk = k;
+    if (vsign(uv) > 0) {
+        if (d == 0) r.di = i == 0 ? g.nx - 1 : i - 1;
+        else if (d == 1) r.dj = j == 0 ? g.ny - 1 : j - 1;
+        else r.dk = k == 0 ? g.nz - 1 : k - 1;
+    }
+    r.donor = cell(r.di, r.dj, r.dk, g);
     return r;
 }
 
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(kFaceTile) k_face_flux_bx(const __grid_constan
         const BoxFace fc = decode_box_face(S, list[(size_t)sgi * cap + (e - off[sgi])], d, uv);
         const BoxDev<T>& B = S.b[fc.box];
         T st[27];
-        gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
+        gather_stencil_ijk(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.di, fc.dj, fc.dk, B.g, st);
         T m[3];
         myc_normal(st, m);
         const T alpha = plic_alpha_banded(m[0], m[1], m[2], st[13], band);

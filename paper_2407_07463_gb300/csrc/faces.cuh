@@ -5,11 +5,10 @@
 
 namespace vof {
 
-// 3x3x3 stencil of cell x (periodic), st[(k+1)*9 + (j+1)*3 + (i+1)].
+// 3x3x3 stencil of cell (i, j, k) (periodic), st[(k+1)*9 + (j+1)*3 + (i+1)].
 template <typename T>
-__device__ __forceinline__ void gather_stencil(const T* __restrict__ cf, int x, const Dims& g, T st[27]) {
-    int i, j, k;
-    decode(x, g, i, j, k);
+__device__ __forceinline__ void gather_stencil_ijk(const T* __restrict__ cf, int i, int j, int k, const Dims& g,
+                                                   T st[27]) {
     int im = i == 0 ? g.nx - 1 : i - 1, ip = i == g.nx - 1 ? 0 : i + 1;
     int jm = j == 0 ? g.ny - 1 : j - 1, jp = j == g.ny - 1 ? 0 : j + 1;
     int km = k == 0 ? g.nz - 1 : k - 1, kp = k == g.nz - 1 ? 0 : k + 1;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128, 4) k_face_normals_net(const __grid_consta
             const BoxFace fc = decode_box_face(S, list[(size_t)sgi * cap + (e - off[sgi])], d, uv);
             const BoxDev<float>& B = S.b[fc.box];
             dst = B.net + fc.t;
-            gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
+            gather_stencil_ijk(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.di, fc.dj, fc.dk, B.g, st);
         } else {
 #pragma unroll
             for (int q = 0; q < 27; ++q) st[q] = 0.5f;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
             sv = uv * B.sfac;
             dst = B.flux + fc.t;
             float st[27];
-            gather_stencil(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.donor, B.g, st);
+            gather_stencil_ijk(sweep_in(B, sweep) + (size_t)fc.f * B.g.N, fc.di, fc.dj, fc.dk, B.g, st);
 #pragma unroll
             for (int q = 0; q < 27; ++q) s_st[q][t] = st[q];
             const float4 nv = B.net[fc.t];
