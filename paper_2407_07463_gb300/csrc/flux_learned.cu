@@ -84,14 +84,13 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
     __shared__ float s_enet[128];
     __shared__ int s_list[128];
     __shared__ unsigned char s_myc[128];
-    __shared__ int s_nf;
-    const int t = threadIdx.x;
+    __shared__ int s_wq[4];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int n = off[nseg];
     unsigned n_net = 0, n_myc = 0, n_queued = 0;
     for (int base = blockIdx.x * 128; base < n; base += gridDim.x * 128) {
         const int e = base + t;
         const bool valid = e < n;
-        if (t == 0) s_nf = 0;
         float sv = 0.f, mn[3] = {1.f, 0.f, 0.f};
         bool net_ok = false;
         float* dst = nullptr;
@@ -112,19 +111,28 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
         }
         s_myc[t] = 0;
         __syncthreads();
-        // network residual of every face; the ones above the tolerance queue
+        // network residual of every face; the ones above the tolerance queue,
+        // in face order (a thread then reads the stencil column of its own
+        // face or of one close after it: no bank conflicts when most queue)
         float al = 0.f;
+        bool queue = false;
         if (valid) {
             const float e_net = net_ok ? normal_residual_m<128>(&s_st[0][t], mn, &al) : INFINITY;
-            if (!(e_net <= tol)) {
-                s_enet[t] = e_net;
-                s_list[atomicAdd(&s_nf, 1)] = t;
-            }
+            queue = !(e_net <= tol);
+            s_enet[t] = e_net;
         }
+        const unsigned qb = __ballot_sync(0xffffffffu, queue);
+        if (lane == 0) s_wq[warp] = __popc(qb);
         __syncthreads();
-        if (t == 0) n_queued += s_nf;
+        int q_off = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) q_off += w < warp ? s_wq[w] : 0;
+        const int nq = s_wq[0] + s_wq[1] + s_wq[2] + s_wq[3];
+        if (queue) s_list[q_off + __popc(qb & ((1u << lane) - 1u))] = t;
+        __syncthreads();
+        if (t == 0) n_queued += nq;
         // MYC's normal and residual for the queued faces, on the first threads
-        if (t < s_nf) {
+        if (t < nq) {
             const int u = s_list[t];
             float stl[27], m[3], am;
 #pragma unroll
