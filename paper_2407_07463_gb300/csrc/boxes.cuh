@@ -359,10 +359,11 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
             // A warp whose cells and both neighbours along d are all empty
             // (class 0) and carry no c_c bit has no flux through any face:
             // every cell keeps its value and none is interfacial.
-            bool quiet = ccm == 0 || !ic.valid;
+            bool any_pos = false;
 #pragma unroll
             for (int e = 0; e < VW; ++e)
-                quiet &= !ic.valid || (vclass(cur.cl[e]) | vclass(cur.cx[e]) | vclass(cur.ch[e])) == 0;
+                any_pos |= above_zero(cur.cl[e]) || above_zero(cur.cx[e]) || above_zero(cur.ch[e]);
+            const bool quiet = !ic.valid || (ccm == 0 && !any_pos);
             T v[VW];
             uint32_t flo = 0, fhi = 0;
             int nflag = 0;
@@ -372,17 +373,22 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
                 const T* __restrict__ flux = B.flux + base;
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
-                    const int kl = (lo_nz >> e) & 1u ? vclass((lo_pos >> e) & 1u ? cur.cl[e] : cur.cx[e]) : 0;
-                    const int kh = (hi_nz >> e) & 1u ? vclass((hi_neg >> e) & 1u ? cur.ch[e] : cur.cx[e]) : 0;
+                    // upwind donors through the low and high faces: empty (no
+                    // flux), full (flux s) or interfacial (the listed flux)
+                    const T dl = (lo_pos >> e) & 1u ? cur.cl[e] : cur.cx[e];
+                    const T dh = (hi_neg >> e) & 1u ? cur.ch[e] : cur.cx[e];
+                    const bool ml = ((lo_nz >> e) & 1u) && above_zero(dl);
+                    const bool mh = ((hi_nz >> e) & 1u) && above_zero(dh);
+                    const bool fl = at_least_one(dl), fh = at_least_one(dh);
                     const bool cc = (ccm >> e) & 1u;
-                    T F_lo = kl == 2 ? s_lo[e] : T(0), F_hi = kh == 2 ? s_hi[e] : T(0);
-                    if (kl == 1) F_lo = flux[x0 + e];
-                    if (kh == 1) F_hi = flux[x0 + hi_off(e)];
+                    T F_lo = ml && fl ? s_lo[e] : T(0), F_hi = mh && fh ? s_hi[e] : T(0);
+                    if (ml && !fl) F_lo = flux[x0 + e];
+                    if (mh && !fh) F_hi = flux[x0 + hi_off(e)];
                     // a cell that nothing enters or leaves keeps its bits (signed zero)
-                    if ((kl | kh) != 0 || cc)
+                    if (ml || mh || cc)
                         v[e] = cur.cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi[e] - s_lo[e]);
                     if (PH == 2 && (v[e] < T(0) || v[e] > T(1))) continue;  // clipped below: not interfacial
-                    if (vclass(v[e]) == 1) {
+                    if (above_zero(v[e]) && !at_least_one(v[e])) {
                         flo |= nf_lo & (1u << e);
                         fhi |= nf_hi & (1u << e);
                     }

@@ -84,6 +84,14 @@ __device__ __forceinline__ int vclass(double v) {
 __device__ __forceinline__ int vclass(float v) {
     return v <= 0.f ? 0 : (v >= 1.f ? 2 : 1);
 }
+// The two tests vclass is made of: v > 0 and v >= 1 (integer compares of
+// the bit pattern for double, as there).
+__device__ __forceinline__ bool above_zero(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool above_zero(float v) { return v > 0.f; }
+__device__ __forceinline__ bool at_least_one(double v) {
+    return __double_as_longlong(v) >= 0x3FF0000000000000LL;
+}
+__device__ __forceinline__ bool at_least_one(float v) { return v >= 1.f; }
 __device__ __forceinline__ bool is_exact_zero(double v) {
     return (__double_as_longlong(v) << 1) == 0;
 }
