@@ -116,10 +116,11 @@ Layout layout_for(const vof_config* c) {
     L.size[S_NCMAP] = K * words * 4;
     L.size[S_MVBITS] = K * words * 4;
     L.size[S_LABELS] = K * N * 4;
-    L.size[S_PARENT] = N * 4;
-    L.size[S_RANK] = N * 4;
-    L.size[S_BTOT] = (nb + 1) * 4;
-    L.size[S_BOFF] = (nb + 1) * 4;
+    // labelling scratch, one set per field (Step 2 tags fields side by side)
+    L.size[S_PARENT] = K * N * 4;
+    L.size[S_RANK] = K * N * 4;
+    L.size[S_BTOT] = K * (nb + 1) * 4;
+    L.size[S_BOFF] = K * (nb + 1) * 4;
     L.size[S_PTABLE] = (size_t)kPairCap * 8;
     L.size[S_PLIST] = (size_t)kPairCap * 8;
     L.size[S_MV] = (size_t)(3 * kMaxK + kMoveCap) * 4;
@@ -148,6 +149,8 @@ Layout layout_for(const vof_config* c) {
 
 }  // namespace
 
+constexpr int kSideStreams = 4;
+
 struct vof_ctx {
     vof_config cfg;
     Dims g;
@@ -168,6 +171,18 @@ struct vof_ctx {
     Prof prof;
     const void* mlp;  // borrowed weight blob of the learned normal (VOF_MIXED_LEARNED)
     double mlp_tol;
+    // streams on which the flagged fields of Step 2 are tagged side by side
+    // (forked from and joined back to `stream` by events)
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
+
+    ~vof_ctx() {
+        for (cudaStream_t s : side)
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t e : ev_join)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
 
     template <typename P>
     P* slot(int s) const { return (P*)(ws + L.off[s]); }
@@ -270,19 +285,33 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     VOF_CUDA(ctx, cudaMemsetAsync(table, 0xff, (size_t)kPairCap * 8, st));
     VOF_CUDA(ctx, cudaMemsetAsync(overflow, 0, sizeof(int), st));
     VOF_CUDA(ctx, cudaMemsetAsync(counters + 1, 0, sizeof(unsigned long long), st));
-    for (int f : flagged) {
-        int* lab = labels + (size_t)f * g.N;
-        VOF_CUDA(ctx, timed(ctx, P_LABEL, [&] {
-                     return label_field(bits + (size_t)f * words, g, cf.connectivity, ctx->slot<int>(S_PARENT),
-                                        ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT), ctx->slot<int>(S_BOFF),
-                                        lab, nullptr, 0, nout + f, st, &ctx->launches);
-                 }));
-        VOF_CUDA(ctx, timed(ctx, P_PAIRS, [&] {
-                     return tag_pairs(ncmap + (size_t)f * words, bits + (size_t)f * words, lab, g, cf.stencil_w,
-                                      f, table, kPairCap, overflow, st);
-                 }));
-        ctx->launches += 1;
-    }
+    // the flagged fields are tagged (and their pairs inserted) side by side,
+    // one labelling scratch set each, on the side streams
+    const int nfl = (int)flagged.size();
+    const int nss = std::min(nfl, kSideStreams);
+    const size_t nb = ((size_t)g.N + 1023) / 1024;
+    VOF_CUDA(ctx, timed(ctx, P_LABEL, [&]() -> cudaError_t {
+                 cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+                 for (int i = 0; i < nss && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->side[i], ctx->ev_fork, 0);
+                 for (int i = 0; i < nfl && e == cudaSuccess; ++i) {
+                     const int f = flagged[i];
+                     cudaStream_t ss = ctx->side[i % nss];
+                     int* lab = labels + (size_t)f * g.N;
+                     e = label_field(bits + (size_t)f * words, g, cf.connectivity,
+                                     ctx->slot<int>(S_PARENT) + (size_t)i * g.N, ctx->slot<int>(S_RANK) + (size_t)i * g.N,
+                                     ctx->slot<int>(S_BTOT) + i * (nb + 1), ctx->slot<int>(S_BOFF) + i * (nb + 1), lab,
+                                     nullptr, 0, nout + f, ss, &ctx->launches);
+                     if (e == cudaSuccess)
+                         e = tag_pairs(ncmap + (size_t)f * words, bits + (size_t)f * words, lab, g, cf.stencil_w, f,
+                                       table, kPairCap, overflow, ss);
+                     ctx->launches += 1;
+                 }
+                 for (int i = 0; i < nss && e == cudaSuccess; ++i) {
+                     e = cudaEventRecord(ctx->ev_join[i], ctx->side[i]);
+                     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join[i], 0);
+                 }
+                 return e;
+             }));
     VOF_CUDA(ctx, timed(ctx, P_PAIRS, [&] { return compact_pairs(table, kPairCap, plist, counters + 1, st); }));
     ctx->launches += 1;
     unsigned long long npairs = 0;
@@ -455,6 +484,15 @@ vof_status vof_init(const vof_config* cfg, void* c_dev, const void* u_dev, void*
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_R], 0, L.size[S_HIST_R], ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_RT], 0, L.size[S_HIST_RT], ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_MOM], 0, L.size[S_MOM], ctx->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete ctx;
+        return VOF_ERR_CUDA;
+    }
+    bool made = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < kSideStreams && made; ++i)
+        made = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!made) {
         (void)cudaGetLastError();
         delete ctx;
         return VOF_ERR_CUDA;
