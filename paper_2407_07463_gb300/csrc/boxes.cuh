@@ -172,7 +172,9 @@ __device__ __forceinline__ int warp_reserve(int nflag, int lane, int* s_count) {
 }
 
 // Faces of sweep d whose upwind donor is interfacial (start of a call, or
-// after a recolouring moved drops), from the state c of every box.
+// after a recolouring moved drops), from the state c of every box.  A warp
+// takes one row chunk and walks its fields (the velocity read once), with
+// the next field's loads issued before the current one is tested.
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<T, NB> S, int d,
                                                  unsigned long long* __restrict__ list, long long cap,
@@ -184,35 +186,60 @@ __global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     unsigned long long* seg = list + (size_t)blockIdx.x * cap;
-    for (int it = blockIdx.x * wpb + (threadIdx.x >> 5); it < S.items; it += gridDim.x * wpb) {
-        const int bx = box_of_item(S, it);
+    for (int chk = blockIdx.x * wpb + (threadIdx.x >> 5); chk < S.chunks; chk += gridDim.x * wpb) {
+        const int bx = box_of_chunk(S, chk);
         const BoxDev<T>& B = S.b[bx];
-        const ItemCells ic = item_cells(B, it - B.item0, lane);
-        const T* cf = B.c + (size_t)ic.f * B.g.N;
-        const T* ud = B.u + (size_t)d * B.g.N;
-        T cx[VW], cl[VW], ul[VW];
-        ld16(cf + ic.x0, cx);
-        ld16(ud + ic.x0, ul);
-        if (d == 0) {
-            const T cprev = prev_along_x<T, VW>(cx, cf, ic.x0, ic.i0, B.g.nx, lane);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) cl[e] = e == 0 ? cprev : cx[e - 1];
-        } else {
-            ld16(cf + ic.x0 + (d == 1 ? ic.lo_y : ic.lo_z), cl);
-        }
-        uint32_t fl = 0;
-        int nflag = 0;
+        const Dims& g = B.g;
+        const ItemCells ic = chunk_cells(B, chk - B.chunk0, lane);
+        const int x0 = ic.x0, i0 = ic.i0;
+        const int lo_d = d == 1 ? ic.lo_y : ic.lo_z;
+        const bool need_prev = lane == 0 || i0 == 0;
+        const int xp = i0 == 0 ? x0 + g.nx - 1 : x0 - 1;
+        // faces with a nonzero velocity, and those whose donor is the low cell
+        T ul[VW];
+        ld16(B.u + (size_t)d * g.N + x0, ul);
+        uint32_t nz = 0, pos = 0;
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             const int sg = vsign(ul[e]);
-            const bool flag = ic.valid && sg != 0 && vclass(sg > 0 ? cl[e] : cx[e]) == 1;
-            fl |= (flag ? 1u : 0u) << e;
-            nflag += flag;
+            nz |= (ic.valid && sg != 0 ? 1u : 0u) << e;
+            pos |= (sg > 0 ? 1u : 0u) << e;
         }
-        int pos = warp_reserve(nflag, lane, &s_count);
+        T cx[VW], cl[VW], nx_[VW], nl[VW], pv = T(0), npv = T(0);
+        auto load = [&](int f, T (&x)[VW], T (&l)[VW], T& p) {
+            const T* cf = B.c + (size_t)f * g.N;
+            ld16(cf + x0, x);
+            if (d == 0) p = need_prev ? cf[xp] : T(0);
+            else ld16(cf + x0 + lo_d, l);
+        };
+        load(0, cx, cl, pv);
+        for (int f = 0; f < B.K; ++f) {
+            if (f + 1 < B.K) load(f + 1, nx_, nl, npv);
+            if (d == 0) {
+                T cprev = __shfl_up_sync(0xffffffffu, cx[VW - 1], 1);
+                if (need_prev) cprev = pv;
 #pragma unroll
-        for (int e = 0; e < VW; ++e)
-            if ((fl >> e) & 1u) seg[pos++] = box_face_key(bx, ic.f, ic.i0 + e, ic.j, ic.k);
+                for (int e = 0; e < VW; ++e) cl[e] = e == 0 ? cprev : cx[e - 1];
+            }
+            uint32_t fl = 0;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const T dn = (pos >> e) & 1u ? cl[e] : cx[e];
+                fl |= (((nz >> e) & 1u) && above_zero(dn) && !at_least_one(dn) ? 1u : 0u) << e;
+            }
+            if (__any_sync(0xffffffffu, fl != 0)) {
+                int p = warp_reserve(__popc(fl), lane, &s_count);
+#pragma unroll
+                for (int e = 0; e < VW; ++e)
+                    if ((fl >> e) & 1u) seg[p++] = box_face_key(bx, f, i0 + e, ic.j, ic.k);
+            }
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                cx[e] = nx_[e];
+                cl[e] = nl[e];
+            }
+            pv = npv;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
