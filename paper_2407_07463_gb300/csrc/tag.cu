@@ -63,16 +63,16 @@ __device__ __forceinline__ uint32_t shift_window(uint32_t l, uint32_t c, uint32_
 __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict__ bits,
                                                       uint32_t* __restrict__ ncmap,
                                                       int* __restrict__ flags, Dims g, int K, int w) {
-    long long per_field = (long long)g.rows * g.W;
-    long long words = (long long)K * per_field;
-    long long stride = (long long)gridDim.x * blockDim.x;
+    // one field per blockIdx.y; 32-bit word indices within the field
+    const int per_field = g.rows * g.W;
+    const int f = blockIdx.y;
+    const int stride = gridDim.x * blockDim.x;
     const bool aligned = (g.nx & 31) == 0;
     const bool wide = g.ny > 2 * w && g.nz > 2 * w;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words; idx += stride) {
-        int f = (int)(idx / per_field);
-        long long rem = idx - (long long)f * per_field;
-        int row = (int)(rem / g.W);
-        int wi = (int)(rem - (long long)row * g.W);
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < per_field; rem += stride) {
+        const size_t idx = (size_t)f * per_field + rem;
+        int row = rem / g.W;
+        int wi = rem - row * g.W;
         int j = row % g.ny, k = row / g.ny;
         const uint32_t* fb = bits + (size_t)f * per_field;
         uint32_t centre = fb[(size_t)row * g.W + wi];
@@ -118,14 +118,16 @@ __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict
         }
         uint32_t res = acc & empty;
         if (ncmap) ncmap[idx] = res;
-        if (res) atomicOr(&flags[f], 1);
+        // one atomic per field once it is flagged, not one per word
+        if (res && *(volatile int*)&flags[f] == 0) atomicOr(&flags[f], 1);
     }
 }
 
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
                          cudaStream_t st) {
-    long long words = (long long)K * g.rows * g.W;
-    k_near_contact<<<grid_for(words, 256), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
+    if (K <= 0) return cudaSuccess;
+    const long long per_field = (long long)g.rows * g.W;
+    k_near_contact<<<dim3(grid_for(per_field, 256, 152 * 32 / K + 1), K), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
     return cudaGetLastError();
 }
 
