@@ -11,7 +11,8 @@
 // its network normal (27-cell residual against the tolerance); the faces
 // that need MYC's normal and its residual are compacted to the first
 // threads of the CTA so that the fallback runs on full warps; then every
-// thread takes its plane constant and flux.
+// thread takes its plane constant (the few near c = 0 or 1 refined in FP64,
+// again compacted) and flux.
 #include "boxes.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"
@@ -147,8 +148,8 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
             }
         }
         __syncthreads();
+        float m[3] = {mn[0], mn[1], mn[2]};
         if (valid) {
-            float m[3];
             if (s_myc[t]) {
                 m[0] = s_m[0][t];
                 m[1] = s_m[1][t];
@@ -156,16 +157,36 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
                 al = s_m[3][t];
                 ++n_myc;
             } else {
-                m[0] = mn[0];
-                m[1] = mn[1];
-                m[2] = mn[2];
                 ++n_net;
             }
-            // the residual's FP32 plane constant, refined in FP64 near c = 0 or 1
-            const float cv = s_st[13][t];
-            if (cv < band || cv > 1.f - band) al = plic_alpha_banded(m[0], m[1], m[2], cv, band);
-            *dst = face_flux(m, al, d, sv);
         }
+        // the residual's FP32 plane constant, refined in FP64 near c = 0 or 1:
+        // those faces are compacted to the first threads (in face order), so
+        // that few warps issue the FP64 steps
+        const float cv = s_st[13][t];
+        const bool in_band = valid && (cv < band || cv > 1.f - band);
+        const unsigned bb = __ballot_sync(0xffffffffu, in_band);
+        __syncthreads();  // s_m, s_list and s_wq are free again
+        if (lane == 0) s_wq[warp] = __popc(bb);
+        if (in_band) {
+            s_m[0][t] = m[0];
+            s_m[1][t] = m[1];
+            s_m[2][t] = m[2];
+        }
+        __syncthreads();
+        int b_off = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) b_off += w < warp ? s_wq[w] : 0;
+        const int nb = s_wq[0] + s_wq[1] + s_wq[2] + s_wq[3];
+        if (in_band) s_list[b_off + __popc(bb & ((1u << lane) - 1u))] = t;
+        __syncthreads();
+        if (t < nb) {
+            const int u = s_list[t];
+            s_m[3][u] = plic_alpha_banded(s_m[0][u], s_m[1][u], s_m[2][u], s_st[13][u], band);
+        }
+        __syncthreads();
+        if (in_band) al = s_m[3][t];
+        if (valid) *dst = face_flux(m, al, d, sv);
         __syncthreads();  // the tile's shared arrays are reused by the next tile
     }
     n_net = __reduce_add_sync(0xffffffffu, n_net);
