@@ -140,6 +140,22 @@ def test_normals_fp64(vof):
 # ---------------------------------------------------------------- advection
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_steps_in_several_calls_equal_one_call(vof, precision):
+    """Each call lists the first sweep's faces afresh (k_list_bx), along the
+    step's rotated direction: three one-step calls (lists along x, y, z)
+    end with the same bits as one three-step call (rows of 2 and 4 row
+    chunks)."""
+    c, u, dt, _ = make_case((20, 24, 256), 30, 4.0, seed=21)
+    _, c_one, _, _ = run_gpu(vof, c, u, dt, 3, precision)
+    ctx, c_many, _, _ = run_gpu(vof, c, u, dt, 0, precision)
+    for _ in range(3):
+        ctx.vof_step(dt, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(c_one.cpu().numpy(), c_many.cpu().numpy())
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape,steps", [((32, 32, 32), 1), ((32, 32, 32), 20), ((28, 36, 40), 3),
                                          ((17, 23, 48), 2)])
 def test_advect_fp64_matches_oracle(vof, shape, steps):
