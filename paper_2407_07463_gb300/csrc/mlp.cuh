@@ -37,18 +37,23 @@ struct CanonFrame {
 // canonical frame (reflect so every Youngs component is >= 0, order the axes
 // by increasing |Youngs component|, ties to the lower axis)
 
+// Element i of a 3-array by selects (no local-memory indexing).
+template <typename T>
+__device__ __forceinline__ T pick3(const T v[3], int i) {
+    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
 __device__ __forceinline__ void canon_frame(const float st[27], CanonFrame& fr) {
     float y[3];
     youngs_raw(st, y);
-    float ay[3];
-    for (int a = 0; a < 3; ++a) {
-        fr.sign[a] = y[a] < 0.f ? -1 : 1;
-        ay[a] = fabsf(y[a]);
-    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fr.sign[a] = y[a] < 0.f ? -1 : 1;
+    // the three compares and swaps of a sort of |y| (ties keep the lower axis)
+    float v0 = fabsf(y[0]), v1 = fabsf(y[1]), v2 = fabsf(y[2]), tv;
     int p0 = 0, p1 = 1, p2 = 2, t;
-    if (ay[p1] < ay[p0]) { t = p0; p0 = p1; p1 = t; }
-    if (ay[p2] < ay[p1]) { t = p1; p1 = p2; p2 = t; }
-    if (ay[p1] < ay[p0]) { t = p0; p0 = p1; p1 = t; }
+    if (v1 < v0) { t = p0; p0 = p1; p1 = t; tv = v0; v0 = v1; v1 = tv; }
+    if (v2 < v1) { t = p1; p1 = p2; p2 = t; tv = v1; v1 = v2; v2 = tv; }
+    if (v1 < v0) { t = p0; p0 = p1; p1 = t; }
     fr.perm[0] = p0;
     fr.perm[1] = p1;
     fr.perm[2] = p2;
@@ -56,18 +61,28 @@ __device__ __forceinline__ void canon_frame(const float st[27], CanonFrame& fr) 
 
 // x[q] = canonical stencil value - 1/2, canonical order (k'+1)*9+(j'+1)*3+(i'+1)
 __device__ __forceinline__ void canon_input(const float st[27], const CanonFrame& fr, float x[27]) {
+    const int step[3] = {1, 3, 9};
+    int s[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q] = pick3(fr.sign, fr.perm[q]) * pick3(step, fr.perm[q]);
+#pragma unroll
     for (int kc = -1; kc <= 1; ++kc)
+#pragma unroll
         for (int jc = -1; jc <= 1; ++jc)
+#pragma unroll
             for (int ic = -1; ic <= 1; ++ic) {
-                int o[3] = {0, 0, 0};
-                const int cv[3] = {ic, jc, kc};
-                for (int q = 0; q < 3; ++q) o[fr.perm[q]] = fr.sign[fr.perm[q]] * cv[q];
-                x[(kc + 1) * 9 + (jc + 1) * 3 + (ic + 1)] = VOF_ST(st, o[0], o[1], o[2]) - 0.5f;
+                x[(kc + 1) * 9 + (jc + 1) * 3 + (ic + 1)] = st[13 + ic * s[0] + jc * s[1] + kc * s[2]] - 0.5f;
             }
 }
 
 __device__ __forceinline__ void canon_output(const float nc[3], const CanonFrame& fr, float n[3]) {
-    for (int q = 0; q < 3; ++q) n[fr.perm[q]] = (float)fr.sign[fr.perm[q]] * nc[q];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v = fr.perm[q] == a ? (float)fr.sign[a] * nc[q] : v;
+        n[a] = v;
+    }
 }
 
 // BF16 split of a layer input: x ~ hi + lo with both parts representable
@@ -112,7 +127,7 @@ __device__ __forceinline__ void canon_input_col(const float* col, int stride, co
     const int step[3] = {1, 3, 9};
     int s[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) s[q] = fr.sign[fr.perm[q]] * step[fr.perm[q]];
+    for (int q = 0; q < 3; ++q) s[q] = pick3(fr.sign, fr.perm[q]) * pick3(step, fr.perm[q]);
 #pragma unroll
     for (int kc = -1; kc <= 1; ++kc)
 #pragma unroll

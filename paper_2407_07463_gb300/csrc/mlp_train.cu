@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_train(const MlpBlob* __restrict_
         canon_frame(sv, fr);
         float x[27], tc3[3];
         canon_input(sv, fr, x);
-        for (int q = 0; q < 3; ++q) tc3[q] = (float)fr.sign[fr.perm[q]] * tr[fr.perm[q]];
+        for (int q = 0; q < 3; ++q) tc3[q] = (float)pick3(fr.sign, fr.perm[q]) * pick3(tr, fr.perm[q]);
         for (int q = 0; q < kIn; ++q) store_pair(s.X, t, q, kIn, kInHL, (q < 27 && valid) ? x[q] : 0.f);
         // ---- forward
         publish_smem();
