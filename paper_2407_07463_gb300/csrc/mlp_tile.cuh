@@ -108,13 +108,13 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     tc::fence_after_sync();
     if (t == 0) issue_layer(taddr + kColD1, s.H, kInHL, s.W1, kIn, kHid, &s.bar);
     if (!finish_layer(s, phase)) return false;
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + lane_off + kColD1 + c0, v);
+    for (int c0 = 0; c0 < kHid; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + lane_off + kColD1 + c0, v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + s.b1[c0 + q], 0.f);
-        store_pairs8(s.H, t, c0, kHid, kHidHL, v);
-        store_pairs8(s.H, t, c0 + 8, kHid, kHidHL, v + 8);
+        for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + s.b1[c0 + q], 0.f);
+#pragma unroll
+        for (int k8 = 0; k8 < 32; k8 += 8) store_pairs8(s.H, t, c0 + k8, kHid, kHidHL, v + k8);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -123,13 +123,13 @@ __device__ __forceinline__ bool mlp_tile_forward(MlpSmem& s, uint32_t taddr, uin
     if (t == 0) issue_layer(taddr + kColD2, s.H, kHidHL, s.W2, kHid, kHid, &s.bar);
     if (!finish_layer(s, phase)) return false;
     // layer 2 has finished reading H: its output goes there as layer 3's input
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + lane_off + kColD2 + c0, v);
+    for (int c0 = 0; c0 < kHid; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + lane_off + kColD2 + c0, v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
-        store_pairs8(s.H, t, c0, kHid, kHidHL, v);
-        store_pairs8(s.H, t, c0 + 8, kHid, kHidHL, v + 8);
+        for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + s.b2[c0 + q], 0.f);
+#pragma unroll
+        for (int k8 = 0; k8 < 32; k8 += 8) store_pairs8(s.H, t, c0 + k8, kHid, kHidHL, v + k8);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
