@@ -118,7 +118,12 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
         float al = 0.f;
         bool queue = false;
         if (valid) {
-            const float e_net = net_ok ? normal_residual_m<128>(&s_st[0][t], mn, &al) : INFINITY;
+            float e_net = INFINITY;
+            if (net_ok) {
+                const Residual r = normal_residual_m<128>(&s_st[0][t], mn[0], mn[1], mn[2]);
+                e_net = r.e;
+                al = r.alpha;
+            }
             queue = !(e_net <= tol);
             s_enet[t] = e_net;
         }
@@ -139,7 +144,9 @@ __global__ void __launch_bounds__(128) k_face_flux_judged(const __grid_constant_
 #pragma unroll
             for (int q = 0; q < 27; ++q) stl[q] = s_st[q][u];
             myc_normal(stl, m);
-            if (!(s_enet[u] <= normal_residual_m<128>(&s_st[0][u], m, &am))) {
+            const Residual rm = normal_residual_m<128>(&s_st[0][u], m[0], m[1], m[2]);
+            am = rm.alpha;
+            if (!(s_enet[u] <= rm.e)) {
                 s_m[0][u] = m[0];
                 s_m[1][u] = m[1];
                 s_m[2][u] = m[2];

@@ -22,15 +22,18 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 
 // Residual of an L1-normalised normal m on a stencil: the plane of normal m
 // holding the centre cell's volume fraction, extended over the 3x3x3 block;
-// the mean over the 27 cells of |predicted - actual| fraction.  *alpha gets
-// that plane's constant (FP32).  The reflection and ordering of the normal
+// the mean over the 27 cells of |predicted - actual| fraction, with that
+// plane's constant (FP32).  The reflection and ordering of the normal
 // and the constants of its volume are taken once per stencil; the cells
 // the plane leaves whole cost a compare, the cut ones the piecewise closed
 // form (vol_pw).  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
 // column of a shared-memory tile).
+struct Residual {
+    float e;      // mean |predicted - actual| over the 27 cells
+    float alpha;  // the plane constant
+};
 template <int STRIDE>
-static __device__ __noinline__ float normal_residual_m(const float* st, const float m[3], float* alpha) {
-    const float m0 = m[0], m1 = m[1], m2 = m[2];
+static __device__ __noinline__ Residual normal_residual_m(const float* st, float m0, float m1, float m2) {
     // x_i -> 1 - x_i for a negative component moves the constant by |m_i|
     const float off = fmaxf(-m0, 0.f) + fmaxf(-m1, 0.f) + fmaxf(-m2, 0.f);
     float a = fabsf(m0), b = fabsf(m1), c = fabsf(m2);
@@ -38,7 +41,6 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
     const VolPW p = vol_pw_make(a, b, c);
     // the plane constant in the reflected frame, and in the grid's
     const float A = alpha_pw(p, st[13 * STRIDE]);
-    *alpha = A - off;
     // first pass: the cells the plane leaves whole (volume 0 or 1) cost a
     // compare; the cut ones are collected in a mask and take the volume in a
     // second pass (about a third of the 27 for a plane through the centre)
@@ -60,14 +62,14 @@ static __device__ __noinline__ float normal_residual_m(const float* st, const fl
         const float v = vol_pw(p, A - (m0 * i + m1 * j + m2 * k));
         e += fabsf(v - st[q * STRIDE]);
     }
-    return e * (1.f / 27.f);
+    return {e * (1.f / 27.f), A - off};
 }
 
 // Residual of any normal n (+inf for a zero or non-finite one).
 __device__ __forceinline__ float normal_residual(const float st[27], const float n[3]) {
-    float m[3], al;
+    float m[3];
     if (!l1_normalise(n, m)) return INFINITY;
-    return normal_residual_m<1>(st, m, &al);
+    return normal_residual_m<1>(st, m[0], m[1], m[2]).e;
 }
 
 // The learned normal as the step uses it: the network's normal nn (original
@@ -75,12 +77,12 @@ __device__ __forceinline__ float normal_residual(const float st[27], const float
 // is at most tol, or no larger than that of MYC's normal; otherwise MYC's.
 // m gets the choice; returns true when the network's was kept.
 __device__ __forceinline__ bool judged_normal(const float st[27], const float nn[3], float tol, float m[3]) {
-    float mn[3], al;
-    const float e_net = l1_normalise(nn, mn) ? normal_residual_m<1>(st, mn, &al) : INFINITY;
+    float mn[3];
+    const float e_net = l1_normalise(nn, mn) ? normal_residual_m<1>(st, mn[0], mn[1], mn[2]).e : INFINITY;
     bool keep = e_net <= tol;
     if (!keep) {
         myc_normal(st, m);
-        keep = e_net <= normal_residual_m<1>(st, m, &al);
+        keep = e_net <= normal_residual_m<1>(st, m[0], m[1], m[2]).e;
     }
     if (keep) {
         m[0] = mn[0];

@@ -194,7 +194,7 @@ __device__ __forceinline__ float dvol_pw(const VolPW& p, float alpha) {
 // below (closed forms in regions 1, 2 and the prism, Newton on the cubic in
 // 3 and 4), with products by the normal's constants in place of divisions,
 // then one Newton step on vol_pw.  *region as for alpha_sorted.
-static __device__ __noinline__ float alpha_sorted_pw(const VolPW& p, float v, int* region = nullptr) {
+static __device__ __noinline__ float alpha_sorted_pw(const VolPW p, float v, int* region = nullptr) {
     const float a = p.a, b = p.b, c = p.c;
     if (a <= PlicConst<float>::tiny) {
         // plane parallel to one axis: the 2D area function
