@@ -5,13 +5,14 @@
 // The set travels by value as a __grid_constant__ kernel parameter (about
 // 8 KB for 64 boxes; read in place from the parameter space), so a
 // captured CUDA graph holds it and no table has to be copied to the
-// device.  Work of the update and listing passes is split into items = one
-// 32 * VW-cell chunk of one row of one field of one box (VW cells per lane,
-// 16-byte accesses); items are numbered box by box, row chunk by row chunk,
-// field by field, and the grid walks them in bands of consecutive items so
-// that the fields of a chunk, and the neighbouring rows and planes of a
-// chunk, are read close together in time (L2 reuse of c and u).  The face
-// list of the next sweep holds 64-bit keys box | field | k | j | i.
+// device.  The update and listing passes give a warp one row chunk (32 * VW
+// cells of one row of one box, VW cells per lane, 16-byte accesses) and
+// walk every field of it, so that the chunk's geometry and velocities are
+// taken once; chunks are numbered box by box, row by row, and the grid
+// walks them in bands of consecutive chunks, so that neighbouring rows and
+// planes are read close together in time (L2 reuse of c and u).  Items (one
+// field of a chunk) number the same work field by field within a chunk.
+// The face list of the next sweep holds 64-bit keys box | field | k | j | i.
 #pragma once
 
 #include <algorithm>

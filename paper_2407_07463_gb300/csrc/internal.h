@@ -88,7 +88,10 @@ cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int
 cudaError_t advect_first_sweep_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a);
 cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a);
 // Face-list entries to reserve per list for K fields of grid g (either
-// sweep path, any launch shape the advance may choose).
+// sweep path, any launch shape the advance may choose): a warp of the
+// vectorised passes lists up to 2 faces per cell of every field of each of
+// its row chunks, and the segments of a grid carry the slack of their last
+// chunks.
 inline long long list_reserve(int nx, int ny, int nz, int K, int es) {
     const long long rows = (long long)ny * nz, words = rows * ((nx + 31) / 32);
     const long long scalar = 2LL * 32 * K * (words + kSweepBlocks);
