@@ -285,7 +285,7 @@ SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
                  cudaSuccess ||
              per_sm < 1))
             per_sm = 1;
-        r.gb = std::max(1, std::min(152 * per_sm, kListBlocks / std::max(1, r.wpb / 8)));
+        r.gb = std::max(1, std::min(sm_count() * per_sm, kListBlocks / std::max(1, r.wpb / 8)));
         r.gb = std::min(r.gb, (S.items + r.wpb - 1) / r.wpb);
         r.gb = std::max(r.gb, 1);
         // a warp of the listing pass takes items (one field of a row chunk),
@@ -302,7 +302,7 @@ SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
         const int K = S.b[0].K;
         const int per_sm = std::max(1, std::min(32, 32 / K));
         r.wpb = K;
-        r.gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, 152LL * per_sm));
+        r.gb = (int)std::min<long long>(words, std::min<long long>(kSweepBlocks, (long long)sm_count() * per_sm));
         r.cap = 2LL * 32 * K * ((words + r.gb - 1) / r.gb);
     }
     return r;
@@ -325,7 +325,7 @@ void face_fluxes(const BoxSet<T, NB>& S, int d, int sweep, const unsigned long l
         }
     }
     if (a.prof) a.prof->begin(P_FACE_FLUX);
-    k_face_flux_bx<T, NB><<<152 * 16, kFaceTile, 0, a.stream>>>(S, d, sweep, (T)a.band, list, cap, a.offsets, gb,
+    k_face_flux_bx<T, NB><<<sm_count() * 16, kFaceTile, 0, a.stream>>>(S, d, sweep, (T)a.band, list, cap, a.offsets, gb,
                                                                  a.tile_seg);
     if (a.prof) a.prof->end();
     if (a.launches) *a.launches += 1;

@@ -159,7 +159,28 @@ __device__ __forceinline__ bool bit_at(const uint32_t* __restrict__ bits, int W,
     return (bits[(size_t)row * W + (i >> 5)] >> (i & 31)) & 1u;
 }
 
-inline int grid_for(long long work, int threads, int max_blocks = 152 * 32) {
+// Streaming multiprocessors of the current device, queried once per device
+// (grids are sized in multiples of it); 152 if the query fails.
+inline int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    if (cached[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            (void)cudaGetLastError();
+            v = 152;
+        }
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+inline int grid_for(long long work, int threads, int max_blocks = 0) {
+    if (max_blocks <= 0) max_blocks = sm_count() * 32;
     long long b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > max_blocks) b = max_blocks;

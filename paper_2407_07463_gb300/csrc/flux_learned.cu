@@ -215,7 +215,7 @@ void face_normals_net_set(const BoxSet<float, NB>& S, int d, int sweep, const un
                              (int)sizeof(MlpSmem));
         attr = true;
     }
-    k_face_normals_net<NB><<<152 * 4, 128, sizeof(MlpSmem), st>>>(S, d, sweep, list, cap, off, nseg, tile_seg, w,
+    k_face_normals_net<NB><<<sm_count() * 4, 128, sizeof(MlpSmem), st>>>(S, d, sweep, list, cap, off, nseg, tile_seg, w,
                                                                   status);
 }
 
@@ -223,7 +223,7 @@ template <int NB>
 void face_flux_judged_set(const BoxSet<float, NB>& S, int d, int sweep, float band, const unsigned long long* list,
                           long long cap, const int* off, int nseg, const int* tile_seg, float tol,
                           unsigned long long* counters, cudaStream_t st) {
-    k_face_flux_judged<NB><<<152 * 16, 128, 0, st>>>(S, d, sweep, band, list, cap, off, nseg, tile_seg, tol, counters);
+    k_face_flux_judged<NB><<<sm_count() * 16, 128, 0, st>>>(S, d, sweep, band, list, cap, off, nseg, tile_seg, tol, counters);
 }
 
 #define VOF_LEARNED_SET(NB)                                                                                       \

@@ -54,7 +54,7 @@ constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr int kPairCap = 1 << 16;     // distinct tagged near-contact pairs per call
 constexpr int kMoveCap = 2048;        // moving drops per recolour call
 constexpr int kDropCap = 1 << 20;     // drops over all fields for statistics
-constexpr int kSweepBlocks = 152 * 64; // blocks (and face-list segments) of a sweep
+constexpr int kSweepBlocks = 152 * 64; // most blocks (and face-list segments) of a sweep (buffer capacity)
 
 // Keeps the name of the last CUDA error a library call met (for
 // vof_last_cuda_error); returns the error unchanged.

@@ -163,7 +163,7 @@ cudaError_t learned_normals(const MlpBlob* w, const float* st, float tol, float*
                             long long n, int* status, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     cudaFuncSetAttribute(k_learned_normals, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
-    const int blocks = (int)std::min<long long>((n + 127) / 128, 152LL * 3);
+    const int blocks = (int)std::min<long long>((n + 127) / 128, (long long)sm_count() * 3);
     k_learned_normals<<<blocks, 128, sizeof(MlpSmem), stream>>>(w, st, tol, m_out, which_out, n, status);
     return cudaGetLastError();
 }
@@ -173,7 +173,7 @@ cudaError_t mlp_forward(const MlpBlob* w, const float* st, float* n_out, long lo
     if (n <= 0) return cudaSuccess;
     cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
     long long tiles = (n + 127) / 128;
-    int blocks = (int)std::min<long long>(tiles, 152LL * 4);
+    int blocks = (int)std::min<long long>(tiles, (long long)sm_count() * 4);
     k_mlp_forward<<<blocks, 128, sizeof(MlpSmem), stream>>>(w, st, n_out, n, status);
     return cudaGetLastError();
 }

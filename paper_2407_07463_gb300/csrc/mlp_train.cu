@@ -586,10 +586,10 @@ extern "C" vof_status vof_mlp_train(const vof_train_params* tp, void* weights_de
     } while (0)
     TRY(cudaMemsetAsync(status, 0, 4, st));
     // data
-    k_mlp_gen<<<152 * 16, 128, 0, st>>>(dst, dtg, nullptr, tp->n_train, tp->seed, tp->plane_fraction, tp->r_min,
+    k_mlp_gen<<<sm_count() * 16, 128, 0, st>>>(dst, dtg, nullptr, tp->n_train, tp->seed, tp->plane_fraction, tp->r_min,
                                         tp->r_max);
     if (tp->n_test > 0)
-        k_mlp_gen<<<152 * 16, 128, 0, st>>>(tst, ttg, (float*)(ws + L.test_rad), tp->n_test, host_mix64(tp->seed + 1),
+        k_mlp_gen<<<sm_count() * 16, 128, 0, st>>>(tst, ttg, (float*)(ws + L.test_rad), tp->n_test, host_mix64(tp->seed + 1),
                                             tp->plane_fraction, tp->r_min, tp->r_max);
     TRY(cudaGetLastError());
     // initial weights: He-normal hidden layers (Box-Muller on a counter RNG), zero biases
@@ -647,7 +647,7 @@ extern "C" vof_status vof_mlp_train(const vof_train_params* tp, void* weights_de
         TRY(cudaMemsetAsync(hist, 0, 3 * 18000 * 4, st));
         TRY(cudaMemsetAsync(sums, 0, 32, st));
         TRY(cudaMemsetAsync(ws + L.bins, 0, 5 * 4 * 8, st));
-        k_mlp_eval_angles<<<152 * 8, 128, 0, st>>>(tst, ttg, (const float*)(ws + L.test_rad), tnm, tp->n_test,
+        k_mlp_eval_angles<<<sm_count() * 8, 128, 0, st>>>(tst, ttg, (const float*)(ws + L.test_rad), tnm, tp->n_test,
                                                    1e-3f, hist, hist + 18000, hist + 36000, sums,
                                                    (double*)(ws + L.bins));
         TRY(cudaGetLastError());

@@ -127,7 +127,7 @@ cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, cons
                          cudaStream_t st) {
     if (K <= 0) return cudaSuccess;
     const long long per_field = (long long)g.rows * g.W;
-    k_near_contact<<<dim3(grid_for(per_field, 256, 152 * 32 / K + 1), K), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
+    k_near_contact<<<dim3(grid_for(per_field, 256, sm_count() * 32 / K + 1), K), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
     return cudaGetLastError();
 }
 
