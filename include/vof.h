@@ -161,20 +161,21 @@ vof_status vof_label(vof_ctx *ctx, int32_t field, int32_t *label_dev, int32_t *n
 /*
  * Tagging without allocation (the paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the
- * tags -- code running during CUDA-graph stream capture, plug-ins whose
- * host framework owns every device allocation, loops with a memory budget
- * fixed at start-up).  Same result as vof_label on the field c_dev
- * ([nz][ny][nx], double for VOF_FP64 else float; a cell is occupied iff
- * c > tag_tau evaluated in double) with the given connectivity (6 or 26),
- * written to label_dev (int32, caller-owned); *n_drops_host = number of
- * components.  Needs no context and no workspace: scratch is a fixed device
- * array inside the library (about 3 MB per device, kept until the library
- * is unloaded).  nx*ny*nz must not exceed 262144 (64^3): larger grids return
- * VOF_ERR_CAPACITY before anything is launched.  All calls on a device share
- * that array: calls that may overlap on the GPU race and must be
- * serialised by the caller.  The first call on each device looks the array
- * up (cudaGetSymbolAddress with that device current) and should be made
- * before any stream capture begins.  Synchronises `stream`.
+ * tags -- plug-ins whose host framework owns every device allocation and
+ * passes in only finished buffers, loops whose memory budget is fixed at
+ * start-up).  Same result as vof_label on the field c_dev ([nz][ny][nx],
+ * double for VOF_FP64 else float; a cell is occupied iff c > tag_tau
+ * evaluated in double) with the given connectivity (6 or 26), written to
+ * label_dev (int32, caller-owned); *n_drops_host = number of components.
+ * Needs no context and no workspace and calls no allocator: scratch is a
+ * fixed device array inside the library (about 3 MB per device, kept until
+ * the library is unloaded).  nx*ny*nz must not exceed 262144 (64^3): larger
+ * grids return VOF_ERR_CAPACITY before anything is launched.  All calls on a
+ * device share that array, which keeps the last call's contents (no call
+ * reads a word it did not write first): calls that may overlap on the GPU
+ * race and must be serialised by the caller.  The first call on each device
+ * looks the array up (cudaGetSymbolAddress with that device current) and
+ * should be made before any stream capture begins.  Synchronises `stream`.
  */
 vof_status vof_label_noalloc(const void *c_dev, int32_t precision, int32_t nx, int32_t ny,
                              int32_t nz, double tag_tau, int32_t connectivity,

@@ -3,24 +3,26 @@
 //
 // The ordinary path (vof_label) needs a context, and a context needs a
 // workspace that the caller allocates.  Some callers cannot allocate device
-// memory at the moment they need the tags: code running while a stream is
-// being captured into a CUDA graph (cudaMalloc is not a legal capture
-// operation), plug-ins hosted by a framework that owns every device
-// allocation, or a real-time loop whose memory budget is fixed at start-up.
-// This variant serves them: its scratch (occupancy bits, union-find
+// memory at the moment they need the tags: a plug-in hosted by a framework
+// that owns every device allocation and hands it only finished buffers, or
+// a real-time loop whose memory budget is fixed at start-up and may not
+// grow.  This variant serves them: its scratch (occupancy bits, union-find
 // parents, root ranks, block sums) lives in one file-scope device array of
 // fixed size that the GPU keeps for as long as the library is loaded.
 //
 // Limits and rules:
-//  - at most kNoAllocMaxCells cells (64^3); larger grids get VOF_ERR_CAPACITY;
-//  - the array is shared by every call on a device: calls whose kernels can
-//    overlap on the GPU (other streams, other host threads) race and must be
-//    serialised by the caller;
-//  - every scratch word is written before it is read, so the contents left
-//    by the previous call do not matter and nothing needs clearing;
+//  - at most kNoAllocMaxCells cells (64^3); larger grids get VOF_ERR_CAPACITY
+//    before anything is launched;
+//  - the array is shared by every call on a device and keeps the last call's
+//    contents: calls whose kernels can overlap on the GPU (other streams,
+//    other host threads) race and must be serialised by the caller;
+//  - every scratch word a call reads is written earlier in the same call
+//    (bits by the packing pass, parents and ranks of occupied cells and
+//    roots, every block sum, the count by the scan), so the previous call's
+//    contents never leak into a result and nothing needs clearing;
 //  - the first call on a device looks the array's device address up with
 //    cudaGetSymbolAddress (with that device current); make that first call
-//    before starting any stream capture.
+//    before starting any stream capture on that device.
 #include <mutex>
 
 #include "common.cuh"
