@@ -17,93 +17,126 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 
-def build(force=False):
-    """Compile liboracle.so with gcc (no FMA contraction, so every machine
-    rounds the same way)."""
+def _compile(out, extra, force):
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
            "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (no FMA contraction, so every machine
+    rounds the same way), and liboracle_omp.so, the same source with OpenMP
+    (z-planes of the advection step in parallel; identical results).  The
+    OpenMP build is skipped if the compiler lacks OpenMP."""
+    _compile(_LIB, [], force)
+    try:
+        _compile(_LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB
 
 
-def lib():
-    global _lib
+def lib(omp=False):
+    """The serial oracle, or (omp=True) its OpenMP build; None if that build
+    is unavailable."""
+    global _lib, _lib_omp
     with _lock:
+        if omp:
+            if _lib_omp is None:
+                build()
+                if not os.path.exists(_LIB_OMP):
+                    return None
+                _lib_omp = _declare(C.CDLL(_LIB_OMP))
+            return _lib_omp
         if _lib is None:
             build()
-            L = C.CDLL(_LIB)
-            L.oracle_plic_volume.restype = C.c_double
-            L.oracle_plic_volume.argtypes = [_dp, C.c_double]
-            L.oracle_plic_alpha.restype = C.c_double
-            L.oracle_plic_alpha.argtypes = [_dp, C.c_double]
-            for f in ("oracle_youngs", "oracle_myc"):
-                getattr(L, f).restype = None
-                getattr(L, f).argtypes = [_dp, _dp]
-            L.oracle_centred_column.restype = None
-            L.oracle_centred_column.argtypes = [_dp, C.c_int, _dp]
-            L.oracle_myc_choice.restype = C.c_int
-            L.oracle_myc_choice.argtypes = [_dp]
-            L.oracle_face_flux.restype = C.c_double
-            L.oracle_face_flux.argtypes = [_dp, C.c_double, C.c_int, C.c_double]
-            L.oracle_cell_face_flux.restype = C.c_double
-            L.oracle_cell_face_flux.argtypes = [_dp] + [C.c_int] * 7 + [C.c_double]
-            L.oracle_advect_step.restype = C.c_int
-            L.oracle_advect_step.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
-                                             C.c_double, C.c_double, C.c_int64, _dp]
-            L.oracle_normals.restype = None
-            L.oracle_normals.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp]
-            L.oracle_label.restype = C.c_int64
-            L.oracle_label.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _ip]
-            L.oracle_near_contact.restype = C.c_int
-            L.oracle_near_contact.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
-            L.oracle_near_contact_map.restype = None
-            L.oracle_near_contact_map.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int,
-                                                  C.c_double, _up]
-            L.oracle_near_pairs.restype = C.c_int64
-            L.oracle_near_pairs.argtypes = [_dp, _ip, C.c_int, C.c_int, C.c_int, C.c_int,
-                                            C.c_double, C.c_void_p, C.c_void_p, C.c_int64]
-            L.oracle_recolour.restype = C.c_int
-            L.oracle_recolour.argtypes = [_dp, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
-                                          C.c_int, C.c_int, C.c_double, C.c_int,
-                                          C.POINTER(C.c_int), C.c_void_p, C.c_int]
-            L.oracle_drop_table.restype = None
-            L.oracle_drop_table.argtypes = [_dp, _ip, C.c_int64, C.c_int, C.c_int, C.c_int,
-                                            C.c_double, _dp, _dp]
-            L.oracle_pair_stats.restype = None
-            L.oracle_pair_stats.argtypes = [_dp, C.c_int64, _dp, C.c_int, C.c_int, C.c_double,
-                                            C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp,
-                                            _dp]
-            L.oracle_canon.restype = None
-            L.oracle_canon.argtypes = [_dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
-            L.oracle_mlp_forward.restype = None
-            L.oracle_mlp_forward.argtypes = [_dp, _dp, C.c_int, _dp]
-            L.oracle_normal_residual.restype = C.c_double
-            L.oracle_normal_residual.argtypes = [_dp, _dp]
-            L.oracle_learned_normal.restype = C.c_int
-            L.oracle_learned_normal.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_int, _dp,
-                                                C.POINTER(C.c_int)]
-            L.oracle_advect_step_learned.restype = C.c_int
-            L.oracle_advect_step_learned.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
-                                                     C.c_double, C.c_double, C.c_int64, _dp,
-                                                     C.c_double, C.c_double, C.c_int, _dp,
-                                                     C.POINTER(C.c_int64), C.c_void_p]
-            L.oracle_mlp_loss_grad.restype = C.c_double
-            L.oracle_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp]
-            _lib = L
+            _lib = _declare(C.CDLL(_LIB))
     return _lib
+
+
+def threads(n=0, omp=True):
+    """Threads the OpenMP build uses (n > 0 sets them); 1 without it."""
+    L = lib(omp=omp)
+    return 1 if L is None else int(L.oracle_threads(int(n)))
+
+
+def _declare(L):
+    L.oracle_plic_volume.restype = C.c_double
+    L.oracle_plic_volume.argtypes = [_dp, C.c_double]
+    L.oracle_plic_alpha.restype = C.c_double
+    L.oracle_plic_alpha.argtypes = [_dp, C.c_double]
+    for f in ("oracle_youngs", "oracle_myc"):
+        getattr(L, f).restype = None
+        getattr(L, f).argtypes = [_dp, _dp]
+    L.oracle_centred_column.restype = None
+    L.oracle_centred_column.argtypes = [_dp, C.c_int, _dp]
+    L.oracle_myc_choice.restype = C.c_int
+    L.oracle_myc_choice.argtypes = [_dp]
+    L.oracle_face_flux.restype = C.c_double
+    L.oracle_face_flux.argtypes = [_dp, C.c_double, C.c_int, C.c_double]
+    L.oracle_cell_face_flux.restype = C.c_double
+    L.oracle_cell_face_flux.argtypes = [_dp] + [C.c_int] * 7 + [C.c_double]
+    L.oracle_advect_step.restype = C.c_int
+    L.oracle_advect_step.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_double, C.c_double, C.c_int64, _dp]
+    L.oracle_normals.restype = None
+    L.oracle_normals.argtypes = [_dp, C.c_int, C.c_int, C.c_int, _dp]
+    L.oracle_label.restype = C.c_int64
+    L.oracle_label.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _ip]
+    L.oracle_near_contact.restype = C.c_int
+    L.oracle_near_contact.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
+    L.oracle_near_contact_map.restype = None
+    L.oracle_near_contact_map.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_double, _up]
+    L.oracle_near_pairs.restype = C.c_int64
+    L.oracle_near_pairs.argtypes = [_dp, _ip, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.c_void_p, C.c_void_p, C.c_int64]
+    L.oracle_recolour.restype = C.c_int
+    L.oracle_recolour.argtypes = [_dp, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                  C.c_int, C.c_int, C.c_double, C.c_int,
+                                  C.POINTER(C.c_int), C.c_void_p, C.c_int]
+    L.oracle_drop_table.restype = None
+    L.oracle_drop_table.argtypes = [_dp, _ip, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, _dp, _dp]
+    L.oracle_pair_stats.restype = None
+    L.oracle_pair_stats.argtypes = [_dp, C.c_int64, _dp, C.c_int, C.c_int, C.c_double,
+                                    C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp,
+                                    _dp]
+    L.oracle_canon.restype = None
+    L.oracle_canon.argtypes = [_dp, _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.oracle_mlp_forward.restype = None
+    L.oracle_mlp_forward.argtypes = [_dp, _dp, C.c_int, _dp]
+    L.oracle_normal_residual.restype = C.c_double
+    L.oracle_normal_residual.argtypes = [_dp, _dp]
+    L.oracle_learned_normal.restype = C.c_int
+    L.oracle_learned_normal.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_int, _dp,
+                                        C.POINTER(C.c_int)]
+    L.oracle_advect_step_learned.restype = C.c_int
+    L.oracle_advect_step_learned.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.c_double, C.c_int64, _dp,
+                                             C.c_double, C.c_double, C.c_int, _dp,
+                                             C.POINTER(C.c_int64), C.c_void_p]
+    L.oracle_mlp_loss_grad.restype = C.c_double
+    L.oracle_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp]
+    L.oracle_threads.restype = C.c_int
+    L.oracle_threads.argtypes = [C.c_int]
+    return L
 
 
 def _f64(a):
@@ -155,23 +188,24 @@ def cell_face_flux(c, i, j, k, d, s):
 # --------------------------------------------------------------------------- advection
 
 
-def advect_step(c, u, dt, h, step_index):
-    """One step of every field; returns (c_new, clipped[K])."""
+def advect_step(c, u, dt, h, step_index, omp=False):
+    """One step of every field; returns (c_new, clipped[K]).  omp=True runs
+    the OpenMP build (same result)."""
     c = np.array(c, dtype=np.float64, order="C", copy=True)
     squeeze = c.ndim == 3
     if squeeze:
         c = c[None]
     K, nz, ny, nx = c.shape
     clipped = np.zeros(K)
-    rc = lib().oracle_advect_step(c, _f64(u), nx, ny, nz, K, float(dt), float(h),
-                                  int(step_index), clipped)
+    rc = ((lib(omp=True) if omp else None) or lib()).oracle_advect_step(
+        c, _f64(u), nx, ny, nz, K, float(dt), float(h), int(step_index), clipped)
     if rc != 0:
         raise MemoryError("oracle_advect_step")
     return (c[0] if squeeze else c), clipped
 
 
 def advect_step_learned(c, u, dt, h, step_index, params, tol=1e-3, amb_eps=1e-6, amb_choice=0,
-                        amb_map=None):
+                        amb_map=None, omp=False):
     """One step with the learned normal (MYC fallback); returns (c_new,
     clipped[K], counts) with counts = (faces on the network, on MYC,
     ambiguous decisions resolved by amb_choice).  amb_map (uint8 array of
@@ -183,7 +217,8 @@ def advect_step_learned(c, u, dt, h, step_index, params, tol=1e-3, amb_eps=1e-6,
     K, nz, ny, nx = c.shape
     clipped = np.zeros(K)
     counts = (C.c_int64 * 3)()
-    rc = lib().oracle_advect_step_learned(c, _f64(u), nx, ny, nz, K, float(dt), float(h),
+    L = (lib(omp=True) if omp else None) or lib()
+    rc = L.oracle_advect_step_learned(c, _f64(u), nx, ny, nz, K, float(dt), float(h),
                                           int(step_index), _f64(params), float(tol), float(amb_eps),
                                           int(amb_choice), clipped, counts,
                                           None if amb_map is None else amb_map.ctypes.data)
@@ -207,10 +242,10 @@ def learned_normal(params, st, tol=1e-3, amb_eps=0.0, amb_choice=0):
     return m, which, amb.value
 
 
-def advect(c, u, dt, h, steps, first_step=0):
+def advect(c, u, dt, h, steps, first_step=0, omp=False):
     clipped = 0.0
     for s in range(steps):
-        c, cl = advect_step(c, u, dt, h, first_step + s)
+        c, cl = advect_step(c, u, dt, h, first_step + s, omp=omp)
         clipped = clipped + cl
     return c, clipped
 
@@ -337,8 +372,12 @@ def mlp_canon(st):
 
 
 def mlp_forward(params, x, bf16=True):
+    """Canonical-frame output.  bf16=True: BF16 weights and BF16 (hi, lo)
+    layer inputs, as the tensor cores see them; bf16="weights": BF16 weights,
+    FP64 layer inputs; False: all FP64."""
+    mode = 2 if bf16 == "weights" else int(bool(bf16))
     out = np.zeros(3)
-    lib().oracle_mlp_forward(_f64(params), _f64(x), int(bool(bf16)), out)
+    lib().oracle_mlp_forward(_f64(params), _f64(x), mode, out)
     return out
 
 

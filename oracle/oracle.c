@@ -39,6 +39,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP build (the serial build has one).  The advection
+ * step spreads its z-planes over them; every face flux and every cell update
+ * is computed exactly as in the serial build, so results are identical. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* PLIC volume: clipped unit square areas + divergence theorem              */
@@ -361,8 +379,15 @@ static double cell_face_flux(const double *c, int nx, int ny, int nz, int i, int
         oracle_learned_normal(L->params, st, L->tol, L->amb_eps, 1 - L->amb_choice, m2, NULL);
         double F2 = oracle_face_flux(m2, oracle_plic_alpha(m2, cd), d, s);
         if (fabs(F2 - F) > 1e-7) {
-            L->amb_map[idx3(i, j, k, nx, ny)] = 1;
-            L->amb_map[idx3(si, sj, sk, nx, ny)] = 1;
+            uint8_t *a = L->amb_map + idx3(i, j, k, nx, ny), *b = L->amb_map + idx3(si, sj, sk, nx, ny);
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            *a = 1;
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            *b = 1;
         }
     }
     return F;
@@ -401,12 +426,34 @@ static int advect_step(double *c, const double *u, int nx, int ny, int nz, int K
             const double *ccf = cc + (int64_t)f * N;
             if (L)
                 L->amb_map = L_map ? L_map + (int64_t)f * N : NULL;
-            for (int k = 0; k < nz; ++k)
+            /* the OpenMP build takes z-planes in parallel; each plane keeps
+             * its own face counts, added up afterwards (integer sums) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int k = 0; k < nz; ++k) {
+                learned_cfg Lk, *Lp = NULL;
+                if (L) {
+                    Lk = *L;
+                    Lk.counts[0] = Lk.counts[1] = Lk.counts[2] = 0;
+                    Lp = &Lk;
+                }
                 for (int j = 0; j < ny; ++j)
                     for (int i = 0; i < nx; ++i) {
                         int64_t x = idx3(i, j, k, nx, ny);
-                        F[x] = cell_face_flux(cf, nx, ny, nz, i, j, k, d, ud[x] * sfac, L);
+                        F[x] = cell_face_flux(cf, nx, ny, nz, i, j, k, d, ud[x] * sfac, Lp);
                     }
+                if (L)
+                    for (int q = 0; q < 3; ++q) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        L->counts[q] += Lk.counts[q];
+                    }
+            }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < ny; ++j)
                     for (int i = 0; i < nx; ++i) {
@@ -978,7 +1025,7 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
     mlp_view w = mlp_params(params);
     for (int i = 0; i < MLP_IN; ++i) {
         double v = i < 27 ? x[i] : 0.0;
-        xin[i] = bf16 ? bf16_pair(v) : v;
+        xin[i] = bf16 == 1 ? bf16_pair(v) : v;
     }
     for (int o = 0; o < MLP_HID; ++o) {
         double s = 0.0;
@@ -988,7 +1035,7 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
         }
         a1[o] = s + w.b1[o];
         double h = a1[o] > 0.0 ? a1[o] : 0.0;
-        h1[o] = bf16 ? bf16_pair(h) : h;
+        h1[o] = bf16 == 1 ? bf16_pair(h) : h;
     }
     for (int o = 0; o < MLP_HID; ++o) {
         double s = 0.0;
@@ -998,7 +1045,7 @@ static void mlp_fwd_full(const double *params, const double x[27], int bf16, dou
         }
         a2[o] = s + w.b2[o];
         double h = a2[o] > 0.0 ? a2[o] : 0.0;
-        h2[o] = bf16 ? bf16_pair(h) : h;
+        h2[o] = bf16 == 1 ? bf16_pair(h) : h;
     }
     for (int o = 0; o < 3; ++o) {
         double s = 0.0;

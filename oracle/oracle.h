@@ -61,6 +61,9 @@ void oracle_normals(const double *c, int nx, int ny, int nz, double *m_out);
 int64_t oracle_label(const double *c, int nx, int ny, int nz, double tau,
                      int connectivity, int32_t *label);
 
+/* Threads of the OpenMP build (n > 0 sets them); 1 for the serial build. */
+int oracle_threads(int n);
+
 /* Step 1: 1 if some cell with c <= tau has two opposite cells of its
  * (2w+1)^3 stencil with c > tau. */
 int oracle_near_contact(const double *c, int nx, int ny, int nz, int w,
@@ -111,10 +114,11 @@ void oracle_canon(const double st[27], double x[27], int sign[3], int perm[3]);
 
 /* MLP 27 -> 64 -> 64 -> 3, ReLU.  Weights as the GPU blob in FP32:
  * W1[64][32], W2[64][64], W3[16][64], b1[64], b2[64], b3[16] (flat, in that
- * order; 7312 values).  With bf16 != 0, weights are rounded to BF16 (round
- * to nearest even) and every layer input v (the 27 stencil values and the
- * two hidden activations) becomes hi + lo with hi = bf16(v),
- * lo = bf16(v - hi), as the tensor-core path does; everything else in FP64.
+ * order; 7312 values).  bf16 = 0: everything in FP64.  bf16 = 2: weights
+ * rounded to BF16 (round to nearest even), layer inputs and everything else
+ * in FP64.  bf16 = 1: as 2, and every layer input v (the 27 stencil values
+ * and the two hidden activations) becomes hi + lo with hi = bf16(v),
+ * lo = bf16(v - hi), as the tensor-core path feeds it.
  * out[3] = canonical-frame output. */
 void oracle_mlp_forward(const double *params, const double x[27], int bf16, double out[3]);
 

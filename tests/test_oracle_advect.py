@@ -74,3 +74,28 @@ def test_sweep_order_rotates(oracle):
     c, _ = oracle.advect_step(c0, u, dt, 1.0, 1)
     assert np.array_equal(a, b)
     assert not np.array_equal(a, c)
+
+
+def test_openmp_build_equals_serial(oracle):
+    """The OpenMP build (z-planes in parallel) gives the serial build's
+    step bit for bit, with the same face counts and ambiguity map."""
+    if oracle.lib(omp=True) is None:
+        pytest.skip("no OpenMP build")
+    from helpers import youngs_network
+    shape = (18, 20, 22)
+    cen = synth.rsa_centres(shape, 4.0, 5, seed=8)
+    col, _ = synth.greedy_colours(shape, cen, 4.0, 2)
+    c = synth.coloured_fields(shape, cen, 4.0, col, int(col.max()) + 1)
+    u = synth.solenoidal_velocity(shape, 6, 0.5, 1.0, seed=9)
+    dt = synth.dt_for_cfl(u, 0.3)
+    a, ca = oracle.advect_step(c, u, dt, 1.0, 2)
+    b, cb = oracle.advect_step(c, u, dt, 1.0, 2, omp=True)
+    assert np.array_equal(a, b) and np.array_equal(ca, cb)
+    p = youngs_network(0.02, seed=3)
+    ma = np.zeros(c.shape, dtype=np.uint8)
+    mb = np.zeros(c.shape, dtype=np.uint8)
+    a, ca, na = oracle.advect_step_learned(c, u, dt, 1.0, 1, p, amb_eps=3e-5, amb_map=ma)
+    b, cb, nb = oracle.advect_step_learned(c, u, dt, 1.0, 1, p, amb_eps=3e-5, amb_map=mb, omp=True)
+    assert np.array_equal(a, b) and np.array_equal(ca, cb) and na == nb
+    assert np.array_equal(ma, mb)
+    assert na[0] > 0 and na[1] > 0

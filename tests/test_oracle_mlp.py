@@ -122,3 +122,59 @@ def test_learned_step_with_null_network_is_the_myc_step(oracle):
     b, cb, counts = oracle.advect_step_learned(w.c, w.u, w.dt, 1.0, 1, np.zeros(7312))
     assert np.array_equal(a, b) and np.array_equal(ca, cb)
     assert counts[0] == 0 and counts[1] > 0 and counts[2] == 0
+
+
+def _bf16(a):
+    """Round to the nearest BF16 (ties to even) through FP32 (numpy)."""
+    f = np.asarray(a, dtype=np.float32).copy()
+    b = f.view(np.uint32)
+    b += np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))
+    b &= np.uint32(0xFFFF0000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _fwd_layers(p, x):
+    """FP64 forward with BF16 weights: layer inputs |x|, |h1|, |h2| and the
+    absolute weights, for the error bound below."""
+    W1 = _bf16(p[0:2048].reshape(64, 32)[:, :27])
+    W2 = _bf16(p[2048:6144].reshape(64, 64))
+    W3 = _bf16(p[6144:7168].reshape(16, 64)[:3])
+    b1, b2 = p[7168:7232], p[7232:7296]
+    h1 = np.maximum(W1 @ x + b1, 0.0)
+    h2 = np.maximum(W2 @ h1 + b2, 0.0)
+    return (W1, W2, W3), (np.abs(x), h1, h2)
+
+
+def test_pair_inputs_within_their_error_bound_of_fp64_inputs(oracle):
+    """The (hi, lo) BF16 pair the oracle feeds to every layer carries its
+    value v to within eps |v|, eps = 2^-17: |v - hi| <= 2^-9 |v| (hi = bf16(v)),
+    fl32(v) - hi is exact and lo = bf16 of it adds at most 2^-9 of that,
+    plus 2^-24 |v| from the FP32 conversion.  Propagated through the layers
+    (ReLU is 1-Lipschitz): d1 = |W1| eps|x|, e1 = d1 + eps|h1|,
+    e2 = |W2| e1 + eps|h2|, |d out| <= |W3| e2 (to first order).  The
+    pair-input forward (the tensor cores' arithmetic) must lie within that
+    bound of the forward on exact FP64 inputs with the same BF16 weights (the
+    survey's reading).  A forward that dropped the low halves departs from
+    the FP64-input forward by more than 20 times as much in every trial, so
+    a wrong split would not hide inside the comparison."""
+    rng = np.random.default_rng(11)
+    eps = 2.0 ** -17
+    worst = 0.0
+    for trial in range(60):
+        p = rng.normal(size=oracle.MLP_NPARAM) * (0.2 if trial % 2 else 0.5)
+        x = rng.uniform(-0.5, 0.5, 27)
+        pair = oracle.mlp_forward(p, x, bf16=True)
+        exact = oracle.mlp_forward(p, x, bf16="weights")
+        (W1, W2, W3), (ax, h1, h2) = _fwd_layers(p, x)
+        e1 = np.abs(W1) @ (eps * ax) + eps * h1
+        e2 = np.abs(W2) @ e1 + eps * h2
+        bound = 1.01 * (np.abs(W3) @ e2) + 1e-15
+        assert np.all(np.abs(pair - exact) <= bound), (trial, pair - exact, bound)
+        worst = max(worst, float((np.abs(pair - exact) / bound).max()))
+        # hi parts only: errors of 2^-9 |v| per input, far above the bound
+        hx = _bf16(x)
+        g1 = _bf16(np.maximum(W1 @ hx + p[7168:7232], 0.0))
+        g2 = _bf16(np.maximum(W2 @ g1 + p[7232:7296], 0.0))
+        hi_only = W3 @ g2 + p[7296:7299]
+        assert np.abs(hi_only - exact).max() > 20 * np.abs(pair - exact).max(), trial
+    print("largest share of the bound used by the pair forward:", worst)
