@@ -38,6 +38,7 @@ UNIT = "cell-field updates/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM = 6800.0
+TAG_TAU = 1e-6  # occupancy threshold of Steps 1-4 (the library's default)
 
 
 def parse():
@@ -56,7 +57,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=64, help="sub-box edge of the oracle sample")
+    p.add_argument("--cpu-sample", type=int, default=64, help="sub-box edge of the reference arm's sample")
     p.add_argument("--workload", choices=["box", "batched"], default="box",
                    help="box: 256^3 K=8 (the headline); batched: 64 uneven boxes in one launch per pass")
     p.add_argument("--boxes", type=int, default=64)
@@ -200,38 +201,57 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s"
 
 
-def class_roofline(name, cnt, tot_ms, n_cells, fields, es, rep, learned, hbm, peak_src, sm_mhz, args):
-    """Roofline entry of one kernel class from its live CUDA-event time."""
+def sweep_bytes(n_cells, fields, es):
+    """Algorithmic bytes of one sweep launch: the method's own minimum per
+    step (read and write c once per cell-field, the three velocity
+    components once per cell: 2 es + 3 es / K per cell-field update, 9.5 B
+    at K = 8 in FP32) over the three sweeps of the step."""
+    return step_bytes(n_cells, fields, es) / 3.0
+
+
+def class_roofline(name, cnt, tot_ms, n_cells, fields, es, hbm, peak_src, launches_per_step):
+    """HBM roofline entry of one kernel class from its live CUDA-event time:
+    the units one launch processes (a sweep kernel: one sweep of every
+    cell-field of the step) times the algorithmic bytes per unit, over the
+    average launch duration."""
     avg_s = tot_ms / cnt * 1e-3
-    faces = (rep.get("faces_network", 0) or 0) + (rep.get("faces_myc", 0) or 0)
-    if name == "update":
-        alg = algorithmic_bytes(name, n_cells, fields, es)
-        ach = alg / avg_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
-    if name == "face_flux" and learned and faces:
-        per_launch = faces / cnt
-        judged = (rep.get("faces_myc_judged", 0) or 0) / cnt
-        flops = per_launch * (RESIDUAL_FLOPS + FLUX_FLOPS) + judged * (MYC_FLOPS + RESIDUAL_FLOPS)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        ach = flops / avg_s / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "algorithmic_flops_per_launch": flops,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock)"}
-    if name == "net_normals" and faces:
-        flops = faces / cnt * MLP_FLOPS
-        pk, src = bf16_peak()
-        ach = flops / avg_s / 1e12
-        return {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "algorithmic_flops_per_launch": flops, "peak_source": src}
-    if name in ("list_faces", "pack_bits", "near_contact"):
+    if launches_per_step == 3:
+        alg = sweep_bytes(n_cells, fields, es)
+    else:
         alg = algorithmic_bytes(name, n_cells, fields, es)
         if alg is None:
             return None
-        ach = alg / avg_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
-    return None
+    ach = alg / avg_s / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+
+
+def alu_roofline(cnt, tot_ms, rep, sm_count, sm_mhz):
+    """FP32-issue view of the judged learned flux (an extra key): operations
+    counted from the kernel's formulation over the FP32 lanes of the SMs."""
+    faces = (rep.get("faces_network", 0) or 0) + (rep.get("faces_myc", 0) or 0)
+    if not faces:
+        return None
+    avg_s = tot_ms / cnt * 1e-3
+    per_launch = faces / cnt
+    judged = (rep.get("faces_myc_judged", 0) or 0) / cnt
+    flops = per_launch * (RESIDUAL_FLOPS + FLUX_FLOPS) + judged * (MYC_FLOPS + RESIDUAL_FLOPS)
+    peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ach = flops / avg_s / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "algorithmic_flops_per_launch": flops,
+            "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock)"}
+
+
+def tensor_roofline(cnt, tot_ms, rep):
+    faces = (rep.get("faces_network", 0) or 0) + (rep.get("faces_myc", 0) or 0)
+    if not faces:
+        return None
+    flops = faces / cnt * MLP_FLOPS
+    pk, src = bf16_peak()
+    ach = flops / (tot_ms / cnt * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "algorithmic_flops_per_launch": flops, "peak_source": src}
 
 
 def step_bytes(n_cells, fields, es):
@@ -252,9 +272,10 @@ def train_network(vof, torch, dev, args):
 
 
 def host_network(seed=12345):
-    """He-initialised weights of the same architecture for the oracle's
-    timing sample (the oracle evaluates both estimators and both residuals on
-    every donor, so its cost does not depend on the weights)."""
+    """He-initialised weights of the same architecture (for the oracle's
+    sample when no trained network is at hand; the oracle evaluates both
+    estimators and both residuals on every donor, so its cost hardly depends
+    on the weights)."""
     rng = np.random.default_rng(seed)
     p = np.zeros(7312)
     p[0:2048].reshape(64, 32)[:, :27] = rng.normal(scale=math.sqrt(2 / 27), size=(64, 27))
@@ -263,69 +284,155 @@ def host_network(seed=12345):
     return p
 
 
-def cpu_sample_rate(wl, edge, steps=1, learned=True):
-    """Oracle (single thread) on the sub-box [0, edge)^3 of the workload:
-    one advection step of every active field (learned normal with MYC
-    fallback, or MYC alone), then Steps 1-4."""
+def oracle_sample(c, u, dt, h, k_capacity, params, steps=1, omp=False, first_step=0):
+    """The oracle as it stands on a sub-box: per step one advection step of
+    every active field (learned normal with MYC fallback when params is not
+    None, else MYC), then Steps 1-4.  omp: its OpenMP build over every core
+    this process may use (z-planes of the advection in parallel; the rest is
+    serial).  Returns (updates/s, seconds, updates, threads)."""
     import oracle
 
-    sub = np.ascontiguousarray(wl.c[:wl.k_active, :edge, :edge, :edge])
-    u = np.ascontiguousarray(wl.u[:, :edge, :edge, :edge])
-    params = host_network()
+    oracle.build()
+    threads = 1
+    if omp:
+        threads = oracle.threads(len(os.sched_getaffinity(0)))
+    na = c.shape[0]
     t0 = time.perf_counter()
-    c = sub
-    na = wl.k_active
     for s in range(steps):
-        if learned:
-            c, _, _ = oracle.advect_step_learned(c, u, wl.dt, wl.h, s, params, tol=1e-3)
+        if params is not None:
+            c, _, _ = oracle.advect_step_learned(c, u, dt, h, first_step + s, params, tol=1e-3, omp=omp)
         else:
-            c, _ = oracle.advect_step(c, u, wl.dt, wl.h, s)
-        full = np.zeros((wl.k_capacity,) + c.shape[1:])
+            c, _ = oracle.advect_step(c, u, dt, h, first_step + s, omp=omp)
+        full = np.zeros((k_capacity,) + c.shape[1:])
         full[:na] = c[:na]
-        full, na, _, _, _ = oracle.recolour(full, na, w=2)
+        full, na, _, _, _ = oracle.recolour(full, na, w=2, tau=TAG_TAU)
         c = full[:na]
-    dt = time.perf_counter() - t0
-    updates = edge ** 3 * wl.k_active * steps
-    return updates / dt, dt, updates
+    sec = time.perf_counter() - t0
+    updates = int(np.prod(u.shape[1:])) * sum([c.shape[0]] * steps)
+    return updates / sec, sec, updates, threads
+
+
+def sub_box(wl, edge):
+    return (np.ascontiguousarray(wl.c[:wl.k_active, :edge, :edge, :edge]),
+            np.ascontiguousarray(wl.u[:, :edge, :edge, :edge]))
+
+
+def oracle_sample_child(wl, edge, params, omp):
+    """oracle_sample in a child process (the GPU process keeps its own
+    threading runtime to itself); the inputs travel in a temporary file."""
+    import tempfile
+
+    c, u = sub_box(wl, edge)
+    with tempfile.TemporaryDirectory() as td:
+        f = os.path.join(td, "sample.npz")
+        np.savez(f, c=c, u=u, dt=wl.dt, h=wl.h, k=wl.k_capacity,
+                 params=params if params is not None else np.zeros(0))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", f]
+                           + (["--oracle-omp"] if omp else []), capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_main(path, omp):
+    d = np.load(path)
+    params = d["params"] if d["params"].size else None
+    rate, sec, upd, thr = oracle_sample(d["c"], d["u"], float(d["dt"]), float(d["h"]), int(d["k"]), params,
+                                        omp=omp)
+    print(json.dumps({"rate": rate, "seconds": sec, "updates": upd, "threads": thr}))
+
+
+def cpu_baseline(wl, params, learned):
+    """The oracle timed on this machine's cores: the OpenMP build over every
+    core on a 96^3 sub-box (the reported value) and the serial build on a
+    48^3 sub-box, each one step of every active field plus Steps 1-4."""
+    kind = "learned-normal" if learned else "MYC"
+    res = {}
+    for omp, edge in ((True, min(96, wl.shape[0])), (False, min(48, wl.shape[0]))):
+        try:
+            r = oracle_sample_child(wl, edge, params, omp)
+        except (subprocess.CalledProcessError, OSError, ValueError) as e:
+            res[omp] = {"error": str(e)[:200]}
+            continue
+        res[omp] = {"value": r["rate"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+                    "sample": f"one oracle step ({kind} advection, {'OpenMP over the z-planes' if omp else 'serial'}"
+                              f", then Steps 1-4 serial) of the {edge}^3 sub-box, {wl.k_active} active fields "
+                              f"({r['seconds']:.1f} s)"}
+    out = dict(res[True]) if "value" in res[True] else dict(res[False])
+    out["single_thread"] = res[False]
+    out["cores_available"] = len(os.sched_getaffinity(0))
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on this machine's cores (OpenMP build), on
+    bounded sub-box samples of our arm's workload, same metric."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
     wl = workload(args.n, args.k, args.phi, seed=3)
-    edge = min(args.cpu_sample, 48, args.n)
+    edge = min(args.cpu_sample, args.n)
+    c, u = sub_box(wl, edge)
+    params = host_network()
     for _ in range(args.warmup):
-        cpu_sample_rate(wl, edge)
+        oracle_sample(c, u, wl.dt, wl.h, wl.k_capacity, params, omp=True)
     times = []
     upd = 0
-    for _ in range(args.steps):
-        r, t, u = cpu_sample_rate(wl, edge)
+    thr = 1
+    for s_ in range(args.steps):
+        _, t, n_, thr = oracle_sample(c, u, wl.dt, wl.h, wl.k_capacity, params, omp=True)
         times.append(t)
-        upd += u
+        upd += n_
     total = sum(times)
     value = upd / total
+    sample = (f"{edge}^3 x {wl.k_active} fields sub-box of the workload, one oracle step per timed step "
+              f"(learned-normal advection with He-initialised weights and MYC fallback, OpenMP over the "
+              f"z-planes; Steps 1-4 serial)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_desc(wl),
-                       "sample": f"oracle step (learned-normal advection + Steps 1-4) on the "
-                                 f"{edge}^3 sub-box"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{edge}^3 x {wl.k_active} fields sub-box of the workload, "
-                                       f"one step per timed step (learned normal, He-initialised "
-                                       f"weights, MYC fallback, Steps 1-4)"},
+            "config": {"workload": workload_desc(wl), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- our arm
+
+
+def error_vs_fp64(vof, torch, dev, wl, ref, steps, wts, rbins):
+    """Each FP32 path (MYC; learned when weights are given) advanced from
+    the initial state by `steps` steps with Steps 1-4, against the FP64 path
+    after the same steps (ref): max |dc| per cell-field, max |dC| of the
+    colour sum C = sum_k c_k (independent of which field a drop was moved
+    to), and the relative difference of the total volume."""
+    nz, ny, nx = wl.shape
+    out = {"steps": steps, "against": "plain FP64 GPU path (MYC), same steps from the same state"}
+    runs = [("mixed_myc", vof.VOF_MIXED, None)]
+    if wts is not None:
+        runs.insert(0, ("learned", vof.VOF_MIXED_LEARNED, wts))
+    for name, prec, w in runs:
+        cfg = vof.make_config(nx, ny, nz, k_capacity=wl.k_capacity, k_active=wl.k_active, precision=prec,
+                              recolour=1, stats_rbins=rbins, stats_dr=0.16)
+        c = torch.from_numpy(wl.c).to(dev, torch.float32).contiguous()
+        u = torch.from_numpy(wl.u).to(dev, torch.float32).contiguous()
+        ctx = vof.Context(cfg, c, u)
+        if w is not None:
+            ctx.vof_set_mlp(w, 1e-3)
+        ctx.vof_step(wl.dt, steps)
+        torch.cuda.synchronize()
+        ctx.close()
+        got = c.cpu().numpy().astype(np.float64)
+        del ctx, c, u
+        torch.cuda.empty_cache()
+        out[name] = {"max_abs_per_cell_field": float(np.abs(got - ref).max()),
+                     "max_abs_colour_sum": float(np.abs(got.sum(0) - ref.sum(0)).max()),
+                     "rel_total_volume": float(abs(got.sum() - ref.sum()) / ref.sum())}
+    return out
 
 
 def timed_steps(torch, ctx, dt, steps):
@@ -450,8 +557,12 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": int(c_h.numel() * es), "steps": args.e2e_steps,
                "pipeline": "2 contexts on 2 streams: the copies of one step overlap the next step"}
 
-    # FP64 comparison path on the same workload (plain FP64 kernels)
+    # FP64 comparison path on the same workload (plain FP64 kernels), and the
+    # error of each reduced-precision result against it: every path starts
+    # from the workload's initial state and takes the same steps (with
+    # Steps 1-4), untimed
     fp64 = None
+    err = None
     if not args.no_fp64 and prec != vof.VOF_FP64 and args.fp64_steps > 0:
         del ctx
         torch.cuda.empty_cache()
@@ -464,18 +575,22 @@ def run_ours(args, rank, world):
         ms64, rep64 = timed_steps(torch, ctx64, wl.dt, args.fp64_steps)
         fp64 = {"value": N * rep64["field_steps"] / (ms64 * 1e-3), "unit": UNIT,
                 "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps}
+        ctx64.close()
+        ref = c64.cpu().numpy()
         del ctx64, c64, u64
+        torch.cuda.empty_cache()
+        err = error_vs_fp64(vof, torch, dev, wl, ref, 1 + args.fp64_steps, wts, rbins)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class (and the update pass's HBM one)
+    # roofline of the dominant kernel class against HBM with the method's own
+    # bytes (the ALU and tensor views of the learned kernels as extras)
     hbm, peak_src = peaks()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    roof = None
-    roof_update = None
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     fields = rep["field_steps"] / max(args.steps, 1)
     traffic_tab = {}
     try:
@@ -485,9 +600,10 @@ def run_ours(args, rank, world):
             traffic_tab = tr.get("kernels", {})
     except (OSError, ValueError):
         pass
+    roof = roof_update = roof_alu = roof_tc = None
     for name, (cnt, tot) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        r = class_roofline(name, cnt, tot, N, fields, es, rep, prec == vof.VOF_MIXED_LEARNED, hbm, peak_src,
-                           sm_mhz, args)
+        per_step = round(cnt / max(args.steps, 1))
+        r = class_roofline(name, cnt, tot, N, fields, es, hbm, peak_src, per_step)
         if r is None:
             continue
         r.update({"kernel": name, "launches": cnt, "avg_ms": tot / cnt, "share_of_timed": tot / ms,
@@ -495,21 +611,19 @@ def run_ours(args, rank, world):
         if roof is None:
             roof = r
         if name == "update":
-            roof_update = r
-        if roof is not None and roof_update is not None:
-            break
+            own = algorithmic_bytes("update", N, fields, es)
+            roof_update = dict(r, algorithmic_bytes_per_launch=own, achieved=own / (tot / cnt * 1e-3) / 1e9,
+                               basis="the update pass's own bytes per sweep (c in and out, bits, velocities)")
+            roof_update["frac"] = roof_update["achieved"] / hbm
+        if name == "face_flux" and prec == vof.VOF_MIXED_LEARNED:
+            roof_alu = alu_roofline(cnt, tot, rep, sm_count, sm_mhz)
+        if name == "net_normals":
+            roof_tc = tensor_roofline(cnt, tot, rep)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        import oracle
-
-        oracle.build()
-        edge = min(args.cpu_sample, args.n)
-        r, t, u = cpu_sample_rate(wl, edge, learned=prec == vof.VOF_MIXED_LEARNED)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle step ({'learned-normal' if prec == vof.VOF_MIXED_LEARNED else 'MYC'} "
-                         f"advection + Steps 1-4) of the {edge}^3 sub-box, {wl.k_active} active fields "
-                         f"({t:.1f} s)"}
+        params = vof.mlp_weights_to_params(wts) if wts is not None else None
+        cpu = cpu_baseline(wl, params, prec == vof.VOF_MIXED_LEARNED)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -529,8 +643,8 @@ def run_ours(args, rank, world):
                        "n_active_end": rep["n_active"], "drops_moved": rep["n_moved"],
                        "near_contact_steps": rep["near_contact_steps"]},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "roofline_update_pass": roof_update,
-            "cpu_baseline": cpu, "fp64_path": fp64,
+            "roofline_update_pass": roof_update, "roofline_alu": roof_alu, "roofline_tensor": roof_tc,
+            "cpu_baseline": cpu, "fp64_path": fp64, "error_vs_fp64": err,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
     if fp64:
         line["over_fp64"] = value / world / fp64["value"]
@@ -599,6 +713,9 @@ def run_batched(args, rank, world):
 
 
 def main():
+    if "--oracle-sample" in sys.argv:
+        oracle_sample_main(sys.argv[sys.argv.index("--oracle-sample") + 1], "--oracle-omp" in sys.argv)
+        return
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

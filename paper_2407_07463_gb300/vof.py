@@ -280,6 +280,21 @@ def vof_mlp_params_to_weights(params, weights=None, stream=None):
     return weights
 
 
+def mlp_weights_to_params(weights):
+    """Weight blob (device or host bytes) -> the flat parameters W1[64][32],
+    W2[64][64], W3[16][64], b1[64], b2[64], b3[16] as float64 (7312 values;
+    the BF16 weights are exact in float64).  Host-side unpacking only."""
+    raw = np.asarray(weights.cpu().numpy() if hasattr(weights, "cpu") else weights, dtype=np.uint8)
+    nw = 64 * 32 + 64 * 64 + 16 * 64
+    if raw.size != 2 * nw + 4 * (64 + 64 + 16):
+        raise ValueError("not a weight blob")
+    w16 = raw[:2 * nw].view(np.uint16).astype(np.uint32) << np.uint32(16)
+    out = np.empty(MLP_NPARAM)
+    out[:nw] = w16.view(np.float32)
+    out[nw:] = raw[2 * nw:].view(np.float32)
+    return out
+
+
 def vof_mlp_grad(weights, stencils, targets, stream=None):
     import torch
     g = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=stencils.device)

@@ -71,22 +71,41 @@ def plane_stencils(rng, n):
     return st.astype(np.float32), tg.astype(np.float32)
 
 
+def frame_is_ambiguous(st, rel=1e-5):
+    """The canonical frame (reflections by the signs of the Youngs
+    components, axes ordered by their magnitudes) can flip between FP32 and
+    FP64 when two |components| agree, or one is zero, to within rounding."""
+    y = np.abs(O.youngs(st.astype(np.float64).reshape(3, 3, 3)))
+    ys = np.sort(y)
+    scale = ys[-1] + 1e-300
+    return ys[0] <= rel * scale or (ys[1] - ys[0]) <= rel * scale or (ys[2] - ys[1]) <= rel * scale
+
+
 def test_mlp_forward_matches_oracle(vof):
+    """Elementwise: each normal within 2e-5 of the oracle's (BF16 weights,
+    (hi, lo) BF16 layer inputs, FP64 sums; the GPU sums in FP32), except
+    stencils whose canonical frame sits on a rounding boundary -- counted,
+    at most 1% of them, and those still within 2 degrees."""
     rng = np.random.default_rng(3)
     p = random_params(rng)
     w = vof.vof_mlp_params_to_weights(torch.from_numpy(p.astype(np.float32)).to(DEV))
-    st, _ = plane_stencils(rng, 300)
+    st, _ = plane_stencils(rng, 400)
     st += (rng.random(st.shape) < 0.1) * rng.normal(scale=0.05, size=st.shape).astype(np.float32)
     st = np.clip(st, 0, 1).astype(np.float32)
-    got = vof.vof_mlp_forward(w, torch.from_numpy(st).to(DEV)).cpu().numpy()
+    got = vof.vof_mlp_forward(w, torch.from_numpy(st).to(DEV)).cpu().numpy().astype(np.float64)
     p32 = p.astype(np.float32).astype(np.float64)
-    ang = []
+    worst, boundary = 0.0, 0
     for r in range(len(st)):
         want = O.mlp_normal(p32, st[r].astype(np.float64).reshape(3, 3, 3), bf16=True)
-        ang.append(np.degrees(np.arccos(np.clip(got[r] @ want, -1, 1))))
-    ang = np.array(ang)
-    assert np.median(ang) < 0.05
-    assert ang.max() < 2.0  # BF16 rounding of an activation may differ at a rounding boundary
+        err = float(np.abs(got[r] - want).max())
+        if frame_is_ambiguous(st[r]):
+            boundary += 1
+            assert np.degrees(np.arccos(np.clip(got[r] @ want, -1, 1))) < 2.0
+            continue
+        worst = max(worst, err)
+        assert err <= 2e-5, (r, got[r], want)
+    print("max elementwise error", worst, "frame-boundary stencils", boundary, "of", len(st))
+    assert boundary <= 0.01 * len(st)
 
 
 def test_mlp_gradients_match_oracle(vof):
