@@ -58,8 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=64, help="sub-box edge of the reference arm's sample")
-    p.add_argument("--workload", choices=["box", "batched"], default="box",
-                   help="box: 256^3 K=8 (the headline); batched: 64 uneven boxes in one launch per pass")
+    p.add_argument("--workload", choices=["box", "batched", "nt"], default="box",
+                   help="box: 256^3 K=8 (the headline); batched: 64 uneven boxes in one launch per pass; "
+                        "nt: the tracer-count study N(t) over phi")
     p.add_argument("--boxes", type=int, default=64)
     return p.parse_args()
 
@@ -712,6 +713,48 @@ def run_batched(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_nt(args, rank, world):
+    """Tracer count N(t) under the seeded flow: the synthetic analogue of the
+    paper's N(t) figure (Section 2.3).  For phi in 0.01, 0.05, 0.1, 0.2, N_b =
+    125 drops of diameter 20 cells (d / h = 20) in a box of edge
+    d (N_b pi / (6 phi))^(1/3), coloured greedily, advanced in FP32 (MYC)
+    with Steps 1-4 every step under the 16-mode velocity (amplitude 0.5,
+    vertical drift 1, CFL 0.3); N(t) = fields holding a drop at each step's
+    Step 1.  Not a throughput line: one JSON line of the curves' summaries."""
+    import torch
+
+    from paper_2407_07463_gb300 import synth, vof
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    out = {"study": "tracer count N(t) vs phi under the seeded synthetic flow (analogue of the N(t) figure)",
+           "steps": args.steps, "drops": 125, "d_cells": 20, "cases": []}
+    for phi in (0.01, 0.05, 0.1, 0.2):
+        n = int(round(20.0 * (125 * math.pi / (6.0 * phi)) ** (1.0 / 3.0)))
+        wl = synth.make_workload(f"N(t) phi={phi}", n=n, k_capacity=16, phi=None, n_spheres=125, radius=10.0,
+                                 n_modes=16, amplitude=0.5, drift=1.0, cfl=0.3, seed=40 + int(phi * 100))
+        cfg = vof.make_config(n, n, n, k_capacity=16, k_active=wl.k_active, precision=vof.VOF_MIXED, recolour=1)
+        c = torch.from_numpy(wl.c).to(dev, torch.float32).contiguous()
+        u = torch.from_numpy(wl.u).to(dev, torch.float32).contiguous()
+        ctx = vof.Context(cfg, c, u)
+        series, moved = [], 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = ctx.vof_step(wl.dt, 1)
+            series.append(r["n_in_use"])
+            moved += r["n_moved"]
+        sec = time.perf_counter() - t0
+        ctx.close()
+        series = np.array(series)
+        out["cases"].append({"phi": phi, "edge": n, "k_initial": wl.k_active, "n_max": int(series.max()),
+                             "n_mean": float(series.mean()), "n_final": int(series[-1]), "drops_moved": moved,
+                             "seconds": sec, "series_every_10": series[::10].tolist()})
+        del c, u
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     if "--oracle-sample" in sys.argv:
         oracle_sample_main(sys.argv[sys.argv.index("--oracle-sample") + 1], "--oracle-omp" in sys.argv)
@@ -724,6 +767,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world)
+        return
+    if args.workload == "nt":
+        run_nt(args, rank, world)
         return
     run_ours(args, rank, world)
 

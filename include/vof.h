@@ -71,11 +71,15 @@ typedef struct {
     int32_t stats_rbins;     /* radial bins of the statistics (plus overflow) */
     int32_t stats_tbins;     /* polar bins over [0, pi] */
     double stats_dr;         /* radial bin width (length units) */
+    int32_t stats_every;     /* > 0: vof_step accumulates one statistics event
+                                (vof_stats without the read-back) after every
+                                stats_every-th step of the context (Section 3
+                                samples every 10 steps); 0: off */
 } vof_config;
 
 /* Fill `cfg` with defaults: 32^3, K = 1, FP64, h = 1, w = 2, 6-connectivity,
  * tau = 1e-6, band 1e-3, no recolouring, vertical axis z, 1024 x 150 bins of
- * width 0.2. */
+ * width 0.2, no statistics sampling in vof_step. */
 vof_status vof_config_default(vof_config *cfg);
 
 typedef struct vof_ctx vof_ctx;
@@ -111,6 +115,11 @@ typedef struct {
     int64_t faces_network;     /* VOF_MIXED_LEARNED: interfacial faces on the network's normal */
     int64_t faces_myc;         /* ... and on MYC's normal (the fallback) */
     int64_t faces_myc_judged;  /* faces whose MYC normal and residual were evaluated */
+    int32_t n_in_use;          /* with recolouring: fields holding at least one occupied
+                                  cell at the last step's Step 1, i.e. the tracer count
+                                  N(t) of Section 2.3 (fields left empty by Step 4 are
+                                  free for later moves); -1 without recolouring */
+    int32_t n_in_use_max;      /* largest n_in_use over the call's steps (-1 as above) */
 } vof_step_report;
 
 /*
@@ -203,6 +212,10 @@ typedef struct {
     double M[3];          /* first moment  sum h_ij r / E (accumulated) */
     double R[9];          /* second moment sum h_ij r r^T / E (accumulated) */
     double A[9];          /* R - tr(R)/3 delta */
+    double chi_mean;      /* Appendix A: mean aspect ratio chi_p over all drops of all
+                             accumulated events */
+    double chi_max;       /* largest chi seen */
+    double chi_drops;     /* drops whose chi entered the mean */
 } vof_stats_out;
 
 /*
@@ -213,13 +226,28 @@ typedef struct {
  * and accumulate the events into histograms over r (stats_rbins bins of
  * width stats_dr plus an overflow bin) and over (r, theta) with theta the
  * angle to the vertical axis (stats_tbins bins over [0, pi]), and into the
- * moment sums.  hist_r_host (stats_rbins + 1 doubles) and hist_rt_host
+ * moment sums, and each drop's aspect ratio chi (see vof_drop_shape) into
+ * the running chi_mean / chi_max.  hist_r_host (stats_rbins + 1 doubles) and hist_rt_host
  * ((stats_rbins + 1) * stats_tbins doubles, r-major) receive the accumulated
  * histograms if not NULL.  reset != 0 clears the accumulators first.
  * Synchronises.
  */
 vof_status vof_stats(vof_ctx *ctx, int32_t reset, vof_stats_out *out, double *hist_r_host,
                      double *hist_rt_host);
+
+/*
+ * Drop shape (Appendix A): the inertia tensor of each drop about its centre
+ * of mass, I = integral over the drop of [(r.r) delta - r r], r = x - x_cen
+ * under the minimum image, for the drop's colour density (each cell of the
+ * tag holding its c uniformly: the cell-centre term plus the cube's own
+ * c h^5 / 6 on the diagonal), and its aspect ratio chi = sqrt(I_1 / I_2)
+ * with I_1, I_2 the largest and smallest eigenvalues.  label_dev: this
+ * field's tags (vof_label), cen_dev [n][3] the centroids of vof_drop_table;
+ * inertia_dev [n][6] (double) receives xx yy zz xy xz yz, chi_dev [n]
+ * (double, may be NULL) chi.  Asynchronous.
+ */
+vof_status vof_drop_shape(vof_ctx *ctx, int32_t field, const int32_t *label_dev, int32_t n_labels,
+                          const double *cen_dev, double *inertia_dev, double *chi_dev);
 
 /* Per-drop table of one field given its labels: vol_dev[n] (double) and
  * cen_dev[n][3] (double, x y z in [0, L h)).  Section 2.3 (drop properties

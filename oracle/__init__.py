@@ -134,6 +134,9 @@ def _declare(L):
                                              C.POINTER(C.c_int64), C.c_void_p]
     L.oracle_mlp_loss_grad.restype = C.c_double
     L.oracle_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp]
+    L.oracle_drop_inertia.restype = None
+    L.oracle_drop_inertia.argtypes = [_dp, _ip, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, _dp,
+                                      _dp, _dp]
     L.oracle_threads.restype = C.c_int
     L.oracle_threads.argtypes = [C.c_int]
     return L
@@ -318,6 +321,20 @@ def drop_table(c, lab, n_labels, h=1.0):
     lib().oracle_drop_table(_f64(c), np.ascontiguousarray(lab, dtype=np.int32), int(n_labels),
                             nx, ny, nz, float(h), vol, cen)
     return vol[:n_labels], cen[:n_labels]
+
+
+def drop_inertia(c, lab, n_labels, cen=None, h=1.0):
+    """(inertia[n][6] = xx yy zz xy xz yz, chi[n]) of the drops of one field
+    (Appendix A); centroids from drop_table unless given."""
+    nz, ny, nx = c.shape
+    if cen is None:
+        _, cen = drop_table(c, lab, n_labels, h)
+    I = np.zeros((max(n_labels, 1), 6))
+    chi = np.zeros(max(n_labels, 1))
+    lib().oracle_drop_inertia(_f64(c), np.ascontiguousarray(lab, dtype=np.int32), int(n_labels), nx, ny, nz,
+                              float(h), _f64(np.asarray(cen).reshape(-1, 3) if n_labels else np.zeros((1, 3))),
+                              I, chi)
+    return I[:n_labels], chi[:n_labels]
 
 
 class PairStats:

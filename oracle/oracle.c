@@ -872,6 +872,84 @@ void oracle_drop_table(const double *c, const int32_t *label, int64_t n_labels, 
     free(s1);
 }
 
+/* Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations (each
+ * rotation zeroes one off-diagonal entry; sweeps until the off-diagonal part
+ * is below 1e-15 of the norm).  a is overwritten; w receives the diagonal. */
+static void jacobi_eig3(double a[3][3], double w[3])
+{
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        double nrm = off + a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-30 * nrm)
+            break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0)
+                    continue;
+                /* angle with tan(2 theta) = 2 a_pq / (a_qq - a_pp) */
+                double th = 0.5 * atan2(2.0 * a[p][q], a[q][q] - a[p][p]);
+                double cs = cos(th), sn = sin(th);
+                for (int k = 0; k < 3; ++k) { /* columns p, q */
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = cs * akp - sn * akq;
+                    a[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 3; ++k) { /* rows p, q */
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = cs * apk - sn * aqk;
+                    a[q][k] = sn * apk + cs * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i)
+        w[i] = a[i][i];
+}
+
+void oracle_drop_inertia(const double *c, const int32_t *label, int64_t n_labels, int nx, int ny,
+                         int nz, double h, const double *cen, double *inertia, double *chi)
+{
+    int L[3] = {nx, ny, nz};
+    memset(inertia, 0, sizeof(double) * 6 * (size_t)n_labels);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t x = idx3(i, j, k, nx, ny);
+                int32_t l = label[x];
+                if (l <= 0 || l > n_labels)
+                    continue;
+                int pc[3] = {i, j, k};
+                double r[3];
+                for (int a = 0; a < 3; ++a) {
+                    double Lh = (double)L[a] * h;
+                    double t = ((double)pc[a] + 0.5) * h - cen[3 * (l - 1) + a];
+                    /* minimum image (the drop is smaller than half the box) */
+                    while (t > 0.5 * Lh)
+                        t -= Lh;
+                    while (t < -0.5 * Lh)
+                        t += Lh;
+                    r[a] = t;
+                }
+                double w = c[x] * h * h * h;
+                double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                double own = h * h / 6.0; /* the cell's own moment: its fluid fills the cube */
+                double *I = inertia + 6 * (size_t)(l - 1);
+                I[0] += w * (rr - r[0] * r[0] + own);
+                I[1] += w * (rr - r[1] * r[1] + own);
+                I[2] += w * (rr - r[2] * r[2] + own);
+                I[3] -= w * r[0] * r[1];
+                I[4] -= w * r[0] * r[2];
+                I[5] -= w * r[1] * r[2];
+            }
+    for (int64_t l = 0; l < n_labels; ++l) {
+        const double *I = inertia + 6 * (size_t)l;
+        double a[3][3] = {{I[0], I[3], I[4]}, {I[3], I[1], I[5]}, {I[4], I[5], I[2]}};
+        double w[3];
+        jacobi_eig3(a, w);
+        double mx = fmax(w[0], fmax(w[1], w[2])), mn = fmin(w[0], fmin(w[1], w[2]));
+        chi[l] = mn > 0.0 ? sqrt(mx / mn) : INFINITY;
+    }
+}
+
 void oracle_pair_stats(const double *cen, int64_t n, const double box[3], int vertical_axis,
                        int n_rbins, double dr, int n_tbins, double dtheta, double tie_tol,
                        double *hist_r, double *hist_rt, double *msum, double *rsum,

@@ -94,6 +94,17 @@ void oracle_drop_table(const double *c, const int32_t *label,
                        int64_t n_labels, int nx, int ny, int nz, double h,
                        double *vol, double *cen);
 
+/* Appendix A (deformation): inertia tensor of each drop about its centre of
+ * mass, I = integral over the drop of [(r.r) delta - r r], r = x - x_cen
+ * under the minimum image, with cen[n][3] from oracle_drop_table.  The
+ * fluid of cell q (volume c_q h^3) is taken as filling the cube uniformly
+ * about the cell centre, which adds c_q h^5 / 6 to each diagonal entry
+ * (exact for full cells).  inertia[n][6] = (xx, yy, zz, xy, xz, yz);
+ * chi[n] = sqrt(I_1 / I_2), I_1 and I_2 the largest and smallest
+ * eigenvalues (Jacobi rotations). */
+void oracle_drop_inertia(const double *c, const int32_t *label, int64_t n_labels, int nx, int ny,
+                         int nz, double h, const double *cen, double *inertia, double *chi);
+
 /* Nearest-particle statistics (Section 3): for every particle, its nearest
  * neighbours under the minimum image (ties within tie_tol share weight
  * 1/N_i), histograms of r and (r, theta), first and second moment sums.

@@ -42,6 +42,7 @@ enum Slot {
     S_HIST_R,
     S_HIST_RT,
     S_MOM,
+    S_SHAPE,
     S_NET,
     S_TILESEG,
     S_COUNT
@@ -85,6 +86,7 @@ bool config_valid(const vof_config* c) {
     if (c->stats_rbins < 1 || c->stats_rbins > (1 << 20)) return false;
     if (c->stats_tbins < 1 || c->stats_tbins > 4096) return false;
     if (!(c->stats_dr > 0.0)) return false;
+    if (c->stats_every < 0) return false;
     return true;
 }
 
@@ -134,6 +136,8 @@ Layout layout_for(const vof_config* c) {
     L.size[S_HIST_R] = (size_t)(c->stats_rbins + 1) * 8;
     L.size[S_HIST_RT] = (size_t)(c->stats_rbins + 1) * c->stats_tbins * 8;
     L.size[S_MOM] = 16 * 8;
+    // per-drop inertia tensor (6) and aspect ratio (1) for the statistics
+    L.size[S_SHAPE] = (size_t)kDropCap * 7 * 8;
     // network normal at the cell of every listed face (learned normal only)
     L.size[S_NET] = c->precision == VOF_MIXED_LEARNED ? K * N * 16 : 0;
     // first segment of each tile of kFaceTile entries of a face list
@@ -164,6 +168,7 @@ struct vof_ctx {
     Layout L;
     cudaStream_t stream;
     int n_active;
+    int n_in_use = -1;  // fields holding a drop at the last Step 1 (-1: not measured)
     long long step;
     double umax;
     vof_status sticky;
@@ -270,8 +275,12 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     VOF_CUDA(ctx, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     VOF_CUDA(ctx, cudaStreamSynchronize(st));
     std::vector<int> flagged;
-    for (int f = 0; f < na0; ++f)
-        if (hflags[f]) flagged.push_back(f);
+    int in_use = 0;
+    for (int f = 0; f < na0; ++f) {
+        if (hflags[f] & 1) flagged.push_back(f);
+        in_use += (hflags[f] & 2) ? 1 : 0;
+    }
+    ctx->n_in_use = in_use;
     if (flagged.empty()) return VOF_OK;
     if (fired_out) *fired_out = 1;
 
@@ -423,6 +432,65 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     return status;
 }
 
+// One statistics event (Section 3) of every active field into the context's
+// accumulators: tags, drop volumes and centroids, the drops' inertia
+// tensors and aspect ratios (Appendix A; sum, count and maximum of chi in
+// the moments slot), then the nearest-particle histograms and moments.
+// Synchronises.  *D_out / *vtot_out: drops and their total volume.
+vof_status stats_accumulate(vof_ctx* ctx, long long* D_out, double* vtot_out) {
+    const Dims& g = ctx->g;
+    const vof_config& cf = ctx->cfg;
+    cudaStream_t st = ctx->stream;
+    size_t words = (size_t)g.rows * g.W;
+    double* hr = ctx->slot<double>(S_HIST_R);
+    double* hrt = ctx->slot<double>(S_HIST_RT);
+    double* mom = ctx->slot<double>(S_MOM);
+    uint32_t* bits = ctx->slot<uint32_t>(S_BITS);
+    int* labels = ctx->slot<int>(S_LABELS);
+    int* nout = (int*)(ctx->misc() + kMiscNout);
+    double* S = ctx->slot<double>(S_DSUM);
+    double* cen = ctx->slot<double>(S_CEN);
+    double* vol = ctx->slot<double>(S_VOL);
+    double* shape = ctx->slot<double>(S_SHAPE);  // [D][6] tensors, then [D] chi
+    int* root = ctx->slot<int>(S_ROOT);
+    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, occupancy_tau(ctx), st));
+    ctx->launches += 1;
+    long long D = 0;
+    for (int f = 0; f < ctx->n_active; ++f) {
+        const char* cfp = (const char*)ctx->c + (size_t)f * g.N * ctx->es;
+        int* lab = labels + (size_t)f * g.N;
+        VOF_CUDA(ctx, label_field(bits + (size_t)f * words, g, cf.connectivity, ctx->slot<int>(S_PARENT),
+                                  ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT), ctx->slot<int>(S_BOFF), lab,
+                                  root + D, (int)(kDropCap - D), nout + f, st, &ctx->launches));
+        int n = 0;
+        VOF_CUDA(ctx, cudaMemcpyAsync(&n, nout + f, 4, cudaMemcpyDeviceToHost, st));
+        VOF_CUDA(ctx, cudaStreamSynchronize(st));
+        if (D + n > kDropCap) return VOF_ERR_CAPACITY;
+        if (n > 0) {
+            VOF_CUDA(ctx, cudaMemsetAsync(S + 4 * D, 0, (size_t)n * 4 * 8, st));
+            VOF_CUDA(ctx, drop_sums(cfp, ctx->fp64, lab, ctx->slot<int>(S_PARENT), g, S + 4 * D, n, st));
+            VOF_CUDA(ctx, drop_finalize(S + 4 * D, root + D, g, cf.h, n, vol + D, cen + 3 * D, st));
+            VOF_CUDA(ctx, drop_inertia(cfp, ctx->fp64, lab, g, cf.h, cen + 3 * D, n, shape + 6 * D, st));
+            ctx->launches += 4;
+        }
+        D += n;
+    }
+    VOF_CUDA(ctx, drop_chi(shape, (int)D, shape + 6 * (size_t)kDropCap, mom + 13, st));
+    std::vector<double> hvol((size_t)D);
+    if (D) VOF_CUDA(ctx, cudaMemcpyAsync(hvol.data(), vol, (size_t)D * 8, cudaMemcpyDeviceToHost, st));
+    VOF_CUDA(ctx, cudaStreamSynchronize(st));
+    double vtot = 0.0;
+    for (double v : hvol) vtot += v;
+    double dd = D ? std::cbrt(6.0 * (vtot / (double)D) / M_PI) : 0.0;
+    double Lx = g.nx * cf.h, Ly = g.ny * cf.h, Lz = g.nz * cf.h;
+    VOF_CUDA(ctx, pair_stats(cen, D, Lx, Ly, Lz, cf.vertical_axis, cf.stats_rbins, cf.stats_dr, cf.stats_tbins,
+                             M_PI / cf.stats_tbins, 1e-12 * dd, hr, hrt, mom, st));
+    ctx->launches += 2;
+    if (D_out) *D_out = D;
+    if (vtot_out) *vtot_out = vtot;
+    return VOF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -444,6 +512,7 @@ vof_status vof_config_default(vof_config* cfg) {
     cfg->stats_rbins = 1024;
     cfg->stats_tbins = 150;
     cfg->stats_dr = 0.2;
+    cfg->stats_every = 0;
     return VOF_OK;
 }
 
@@ -592,12 +661,14 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
     a.mlp_counters = mlp_counters;
     a.update_warps = 0;
     a.update_blocks_per_sm = 0;
-    int moved_total = 0, fired_steps = 0;
+    int moved_total = 0, fired_steps = 0, in_use_max = -1;
     long long field_steps = 0;
     vof_status result = VOF_OK;
-    int chunk = ctx->cfg.recolour ? 1 : nsteps;
-    for (int done = 0; done < nsteps; done += chunk) {
-        int n = std::min(chunk, nsteps - done);
+    const int every = ctx->cfg.stats_every;
+    for (int done = 0; done < nsteps;) {
+        // one step at a time with Steps 1-4, and never past a sampling step
+        int n = ctx->cfg.recolour ? 1 : nsteps - done;
+        if (every > 0) n = std::min(n, every - (int)(ctx->step % every));
         a.step = ctx->step;
         field_steps += (long long)ctx->n_active * n;
         if (ctx->fp64) {
@@ -617,7 +688,15 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
             if (moved) a.list_valid = false;  // moves change the interfacial donors
             moved_total += moved;
             fired_steps += fired;
+            in_use_max = std::max(in_use_max, ctx->n_in_use);
         }
+        // statistics events every `every` steps (Section 3 samples them every
+        // 10 steps), accumulated into the context's histograms and moments
+        if (every > 0 && ctx->step % every == 0) {
+            vof_status r = stats_accumulate(ctx, nullptr, nullptr);
+            if (r != VOF_OK) return r;
+        }
+        done += n;
     }
     if (report) {
         double hc[kMaxK];
@@ -639,6 +718,8 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
         report->n_moved = moved_total;
         report->near_contact_steps = fired_steps;
         report->field_steps = field_steps;
+        report->n_in_use = ctx->cfg.recolour ? ctx->n_in_use : -1;
+        report->n_in_use_max = in_use_max;
     }
     return result;
 }
@@ -658,7 +739,7 @@ vof_status vof_near_contact(vof_ctx* ctx, int32_t* flags_host) {
     int h[kMaxK];
     VOF_CUDA(ctx, cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     VOF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int f = 0; f < ctx->cfg.k_capacity; ++f) flags_host[f] = f < ctx->n_active ? (h[f] != 0) : 0;
+    for (int f = 0; f < ctx->cfg.k_capacity; ++f) flags_host[f] = f < ctx->n_active ? (h[f] & 1) : 0;
     return VOF_OK;
 }
 
@@ -727,7 +808,6 @@ vof_status vof_stats(vof_ctx* ctx, int32_t reset, vof_stats_out* out, double* hi
     const Dims& g = ctx->g;
     const vof_config& cf = ctx->cfg;
     cudaStream_t st = ctx->stream;
-    size_t words = (size_t)g.rows * g.W;
     double* hr = ctx->slot<double>(S_HIST_R);
     double* hrt = ctx->slot<double>(S_HIST_RT);
     double* mom = ctx->slot<double>(S_MOM);
@@ -736,44 +816,12 @@ vof_status vof_stats(vof_ctx* ctx, int32_t reset, vof_stats_out* out, double* hi
         VOF_CUDA(ctx, cudaMemsetAsync(hrt, 0, ctx->L.size[S_HIST_RT], st));
         VOF_CUDA(ctx, cudaMemsetAsync(mom, 0, ctx->L.size[S_MOM], st));
     }
-    uint32_t* bits = ctx->slot<uint32_t>(S_BITS);
-    int* labels = ctx->slot<int>(S_LABELS);
-    int* nout = (int*)(ctx->misc() + kMiscNout);
-    double* S = ctx->slot<double>(S_DSUM);
-    double* cen = ctx->slot<double>(S_CEN);
-    double* vol = ctx->slot<double>(S_VOL);
-    int* root = ctx->slot<int>(S_ROOT);
-    VOF_CUDA(ctx, pack_bits(ctx->c, ctx->fp64, bits, g, ctx->n_active, occupancy_tau(ctx), st));
-    ctx->launches += 1;
     long long D = 0;
-    for (int f = 0; f < ctx->n_active; ++f) {
-        const char* cfp = (const char*)ctx->c + (size_t)f * g.N * ctx->es;
-        int* lab = labels + (size_t)f * g.N;
-        VOF_CUDA(ctx, label_field(bits + (size_t)f * words, g, cf.connectivity, ctx->slot<int>(S_PARENT),
-                                  ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT), ctx->slot<int>(S_BOFF), lab,
-                                  root + D, (int)(kDropCap - D), nout + f, st, &ctx->launches));
-        int n = 0;
-        VOF_CUDA(ctx, cudaMemcpyAsync(&n, nout + f, 4, cudaMemcpyDeviceToHost, st));
-        VOF_CUDA(ctx, cudaStreamSynchronize(st));
-        if (D + n > kDropCap) return VOF_ERR_CAPACITY;
-        if (n > 0) {
-            VOF_CUDA(ctx, cudaMemsetAsync(S + 4 * D, 0, (size_t)n * 4 * 8, st));
-            VOF_CUDA(ctx, drop_sums(cfp, ctx->fp64, lab, ctx->slot<int>(S_PARENT), g, S + 4 * D, n, st));
-            VOF_CUDA(ctx, drop_finalize(S + 4 * D, root + D, g, cf.h, n, vol + D, cen + 3 * D, st));
-            ctx->launches += 2;
-        }
-        D += n;
-    }
-    std::vector<double> hvol((size_t)D);
-    if (D) VOF_CUDA(ctx, cudaMemcpyAsync(hvol.data(), vol, (size_t)D * 8, cudaMemcpyDeviceToHost, st));
-    VOF_CUDA(ctx, cudaStreamSynchronize(st));
     double vtot = 0.0;
-    for (double v : hvol) vtot += v;
+    s = stats_accumulate(ctx, &D, &vtot);
+    if (s != VOF_OK) return s;
     double dd = D ? std::cbrt(6.0 * (vtot / (double)D) / M_PI) : 0.0;
     double Lx = g.nx * cf.h, Ly = g.ny * cf.h, Lz = g.nz * cf.h;
-    VOF_CUDA(ctx, pair_stats(cen, D, Lx, Ly, Lz, cf.vertical_axis, cf.stats_rbins, cf.stats_dr, cf.stats_tbins,
-                             M_PI / cf.stats_tbins, 1e-12 * dd, hr, hrt, mom, st));
-    ctx->launches += 1;
     double hm[16];
     VOF_CUDA(ctx, cudaMemcpyAsync(hm, mom, sizeof(hm), cudaMemcpyDeviceToHost, st));
     if (hist_r_host) VOF_CUDA(ctx, cudaMemcpyAsync(hist_r_host, hr, ctx->L.size[S_HIST_R], cudaMemcpyDeviceToHost, st));
@@ -790,6 +838,24 @@ vof_status vof_stats(vof_ctx* ctx, int32_t reset, vof_stats_out* out, double* hi
     for (int q = 0; q < 9; ++q) out->R[q] = hm[3 + q] / E;
     double tr = out->R[0] + out->R[4] + out->R[8];
     for (int q = 0; q < 9; ++q) out->A[q] = out->R[q] - ((q % 4 == 0) ? tr / 3.0 : 0.0);
+    out->chi_drops = hm[14];
+    out->chi_mean = hm[14] > 0 ? hm[13] / hm[14] : 0.0;
+    out->chi_max = hm[15];
+    return VOF_OK;
+}
+
+vof_status vof_drop_shape(vof_ctx* ctx, int32_t field, const int32_t* label_dev, int32_t n_labels,
+                          const double* cen_dev, double* inertia_dev, double* chi_dev) {
+    vof_status s = check_ctx(ctx);
+    if (s != VOF_OK) return s;
+    if (field < 0 || field >= ctx->cfg.k_capacity || !label_dev || n_labels < 0 || n_labels > kDropCap ||
+        (n_labels > 0 && (!cen_dev || !inertia_dev)))
+        return VOF_ERR_ARG;
+    const char* cf = (const char*)ctx->c + (size_t)field * ctx->g.N * ctx->es;
+    VOF_CUDA(ctx, drop_inertia(cf, ctx->fp64, label_dev, ctx->g, ctx->cfg.h, cen_dev, n_labels, inertia_dev,
+                               ctx->stream));
+    VOF_CUDA(ctx, drop_chi(inertia_dev, n_labels, chi_dev, nullptr, ctx->stream));
+    ctx->launches += 2;
     return VOF_OK;
 }
 

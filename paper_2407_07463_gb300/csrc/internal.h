@@ -109,6 +109,8 @@ constexpr int kFaceTile = 128;
 cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, int tile_cap, cudaStream_t st);
 cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
                       cudaStream_t st);
+// Step 1 per field: flags[f] |= 1 if it fired, |= 2 if the field holds an
+// occupied cell (flags cleared by the caller).
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
                          cudaStream_t st);
 cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
@@ -138,6 +140,13 @@ cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* 
                       double* S, int n_max, cudaStream_t st);
 cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, double h, int n,
                           double* vol, double* cen, cudaStream_t st);
+// Drop shape (Appendix A): I[n][6] = xx yy zz xy xz yz about cen (cleared
+// first), then chi = sqrt(I_max / I_min) per drop (chi may be null) with
+// acc[0] += sum chi, acc[1] += drops, acc[2] = max(acc[2], chi) (acc may be
+// null).
+cudaError_t drop_inertia(const void* cf, bool fp64, const int* label_f, const Dims& g, double h, const double* cen,
+                         int n, double* I, cudaStream_t st);
+cudaError_t drop_chi(const double* I, int n, double* chi, double* acc, cudaStream_t st);
 cudaError_t pair_stats(const double* cen, long long n, double bx, double by, double bz, int vaxis,
                        int n_rbins, double dr, int n_tbins, double dtheta, double tie_tol, double* hist_r,
                        double* hist_rt, double* moments, cudaStream_t st);

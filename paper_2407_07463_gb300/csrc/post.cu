@@ -252,6 +252,112 @@ cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, do
 }
 
 // --------------------------------------------------------------------------
+// Drop shape (Appendix A): inertia tensor of each drop about its centre of
+// mass, I = integral over the drop of [(r.r) delta - r r], of the drop's
+// colour density (each cell of the tag holding c uniformly: the cell-centre
+// term plus the cube's own moment c h^5 / 6 on the diagonal), r under the
+// minimum image; and the aspect ratio chi = sqrt(I_max / I_min).
+
+template <typename T>
+__global__ void k_drop_inertia(const T* __restrict__ cf, const int* __restrict__ label_f, Dims g, double h,
+                               const double* __restrict__ cen, int n_max, double* __restrict__ I) {
+    const double L[3] = {g.nx * h, g.ny * h, g.nz * h};
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
+        const int l = label_f[x];
+        if (l <= 0 || l > n_max) continue;
+        int ijk[3];
+        decode(x, g, ijk[0], ijk[1], ijk[2]);
+        double r[3];
+        for (int a = 0; a < 3; ++a) {
+            double t = ((double)ijk[a] + 0.5) * h - cen[3 * (size_t)(l - 1) + a];
+            if (t > 0.5 * L[a]) t -= L[a];
+            if (t < -0.5 * L[a]) t += L[a];
+            r[a] = t;
+        }
+        const double w = (double)cf[x] * h * h * h;
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], own = h * h / 6.0;
+        double* s = I + 6 * (size_t)(l - 1);
+        atomicAdd(s + 0, w * (rr - r[0] * r[0] + own));
+        atomicAdd(s + 1, w * (rr - r[1] * r[1] + own));
+        atomicAdd(s + 2, w * (rr - r[2] * r[2] + own));
+        atomicAdd(s + 3, -w * r[0] * r[1]);
+        atomicAdd(s + 4, -w * r[0] * r[2]);
+        atomicAdd(s + 5, -w * r[1] * r[2]);
+    }
+}
+
+cudaError_t drop_inertia(const void* cf, bool fp64, const int* label_f, const Dims& g, double h, const double* cen,
+                         int n, double* I, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(I, 0, (size_t)n * 6 * 8, st);
+    if (e != cudaSuccess) return e;
+    if (fp64)
+        k_drop_inertia<double><<<grid_for(g.N, 256), 256, 0, st>>>((const double*)cf, label_f, g, h, cen, n, I);
+    else
+        k_drop_inertia<float><<<grid_for(g.N, 256), 256, 0, st>>>((const float*)cf, label_f, g, h, cen, n, I);
+    return cudaGetLastError();
+}
+
+// Extreme eigenvalues of the symmetric matrix [[a, d, e], [d, b, f], [e, f, c]]:
+// with q = tr/3 and B = (A - q 1)/p, p^2 = tr((A - q 1)^2)/6, the eigenvalues
+// are q + 2 p cos(phi + 2 pi m / 3), m = 0, 1, 2, where cos(3 phi) = det(B)/2
+// (the characteristic polynomial of B is the triple-angle identity).
+__device__ __forceinline__ void sym3_extremes(double a, double b, double c, double d, double e, double f,
+                                              double& lmax, double& lmin) {
+    const double off = d * d + e * e + f * f;
+    const double q = (a + b + c) / 3.0;
+    const double p2 = ((a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * off) / 6.0;
+    if (!(p2 > 0.0)) {
+        lmax = lmin = q;
+        return;
+    }
+    const double p = sqrt(p2);
+    const double B00 = (a - q) / p, B11 = (b - q) / p, B22 = (c - q) / p;
+    const double B01 = d / p, B02 = e / p, B12 = f / p;
+    const double det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+    const double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+    const double phi = acos(r) / 3.0;
+    lmax = q + 2.0 * p * cos(phi);
+    lmin = q + 2.0 * p * cos(phi + 2.0 * M_PI / 3.0);
+}
+
+// chi of every drop; acc[0] += sum of chi, acc[1] += drops, acc[2] = max chi.
+__global__ void __launch_bounds__(128) k_drop_chi(const double* __restrict__ I, int n, double* __restrict__ chi,
+                                                  double* __restrict__ acc) {
+    double sum = 0.0, cnt = 0.0, mx = 0.0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const double* s = I + 6 * (size_t)l;
+        double lmax, lmin;
+        sym3_extremes(s[0], s[1], s[2], s[3], s[4], s[5], lmax, lmin);
+        const double x = lmin > 0.0 ? sqrt(lmax / lmin) : INFINITY;
+        if (chi) chi[l] = x;
+        if (isfinite(x)) {
+            sum += x;
+            cnt += 1.0;
+            mx = fmax(mx, x);
+        }
+    }
+    if (!acc) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+        atomicAdd(acc + 0, sum);
+        atomicAdd(acc + 1, cnt);
+        // positive doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long*>(acc + 2), (unsigned long long)__double_as_longlong(mx));
+    }
+}
+
+cudaError_t drop_chi(const double* I, int n, double* chi, double* acc, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_drop_chi<<<grid_for(n, 128, 1024), 128, 0, st>>>(I, n, chi, acc);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
 // Nearest-particle statistics (Section 3, eq. P_nstij with h_ij = 1/N_i for
 // the N_i equidistant nearest neighbours; histograms of eqs. vec_cond and
 // Ptheta_r; moments M and R of Section 4).

@@ -118,8 +118,10 @@ __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict
         }
         uint32_t res = acc & empty;
         if (ncmap) ncmap[idx] = res;
-        // one atomic per field once it is flagged, not one per word
-        if (res && *(volatile int*)&flags[f] == 0) atomicOr(&flags[f], 1);
+        // one atomic per field once it is flagged, not one per word: bit 0
+        // Step 1 fired, bit 1 the field holds an occupied cell
+        if (res && (*(volatile int*)&flags[f] & 1) == 0) atomicOr(&flags[f], 1);
+        if ((centre & valid) && (*(volatile int*)&flags[f] & 2) == 0) atomicOr(&flags[f], 2);
     }
 }
 

@@ -39,14 +39,16 @@ class vof_config(C.Structure):
                 ("h", C.c_double), ("stencil_w", C.c_int32), ("connectivity", C.c_int32),
                 ("tag_tau", C.c_double), ("alpha_fp64_band", C.c_double),
                 ("recolour", C.c_int32), ("vertical_axis", C.c_int32),
-                ("stats_rbins", C.c_int32), ("stats_tbins", C.c_int32), ("stats_dr", C.c_double)]
+                ("stats_rbins", C.c_int32), ("stats_tbins", C.c_int32), ("stats_dr", C.c_double),
+                ("stats_every", C.c_int32)]
 
 
 class vof_step_report(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("clipped_volume", C.c_double),
                 ("n_active", C.c_int32), ("n_moved", C.c_int32),
                 ("near_contact_steps", C.c_int32), ("field_steps", C.c_int64),
-                ("faces_network", C.c_int64), ("faces_myc", C.c_int64), ("faces_myc_judged", C.c_int64)]
+                ("faces_network", C.c_int64), ("faces_myc", C.c_int64), ("faces_myc_judged", C.c_int64),
+                ("n_in_use", C.c_int32), ("n_in_use_max", C.c_int32)]
 
 
 class vof_box_desc(C.Structure):
@@ -87,7 +89,8 @@ class vof_train_report(C.Structure):
 class vof_stats_out(C.Structure):
     _fields_ = [("n_drops", C.c_int32), ("d", C.c_double), ("n_p", C.c_double),
                 ("volume", C.c_double), ("events", C.c_double), ("M", C.c_double * 3),
-                ("R", C.c_double * 9), ("A", C.c_double * 9)]
+                ("R", C.c_double * 9), ("A", C.c_double * 9), ("chi_mean", C.c_double),
+                ("chi_max", C.c_double), ("chi_drops", C.c_double)]
 
 
 _lib = None
@@ -103,7 +106,7 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals",
            "vof_batch_config_default", "vof_batch_workspace_size", "vof_batch_init", "vof_batch_set_mlp",
            "vof_batch_tune", "vof_batch_step", "vof_batch_report", "vof_batch_destroy",
-           "vof_last_cuda_error", "vof_wait_selftest"]
+           "vof_last_cuda_error", "vof_wait_selftest", "vof_drop_shape"]
 
 
 def lib():
@@ -127,6 +130,7 @@ def lib():
         "vof_recolour": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
         "vof_stats": (C.c_int, [vp, i32, C.POINTER(vof_stats_out), vp, vp]),
         "vof_drop_table": (C.c_int, [vp, i32, vp, i32, vp, vp]),
+        "vof_drop_shape": (C.c_int, [vp, i32, vp, i32, vp, vp, vp]),
         "vof_pair_stats": (C.c_int, [vp, i64, vp, i32, i32, dbl, i32, dbl, dbl, vp, vp, vp, vp]),
         "vof_plic_volume": (C.c_int, [i32, vp, vp, vp, i64, vp]),
         "vof_plic_alpha": (C.c_int, [i32, vp, vp, vp, i64, dbl, vp]),
@@ -408,7 +412,8 @@ class Context:
                 "n_active": rep.n_active, "n_moved": rep.n_moved,
                 "near_contact_steps": rep.near_contact_steps, "field_steps": rep.field_steps,
                 "faces_network": rep.faces_network, "faces_myc": rep.faces_myc,
-                "faces_myc_judged": rep.faces_myc_judged}
+                "faces_myc_judged": rep.faces_myc_judged, "n_in_use": rep.n_in_use,
+                "n_in_use_max": rep.n_in_use_max}
 
     step = vof_step
 
@@ -455,7 +460,8 @@ class Context:
                "vof_stats")
         res = {"n_drops": out.n_drops, "d": out.d, "n_p": out.n_p, "volume": out.volume,
                "events": out.events, "M": np.array(out.M[:]),
-               "R": np.array(out.R[:]).reshape(3, 3), "A": np.array(out.A[:]).reshape(3, 3)}
+               "R": np.array(out.R[:]).reshape(3, 3), "A": np.array(out.A[:]).reshape(3, 3),
+               "chi_mean": out.chi_mean, "chi_max": out.chi_max, "chi_drops": out.chi_drops}
         if histograms:
             res["hist_r"] = hr
             res["hist_rt"] = hrt.reshape(nr + 1, nt)
@@ -468,6 +474,16 @@ class Context:
         _check(lib().vof_drop_table(self.handle, int(field), _ptr(labels), int(n_labels), _ptr(vol),
                                     _ptr(cen)), "vof_drop_table")
         return vol[:n_labels], cen[:n_labels]
+
+    def vof_drop_shape(self, field, labels, n_labels, cen):
+        """(inertia [n][6] = xx yy zz xy xz yz, chi [n]) of the drops of a
+        field given its labels and centroids (vof_drop_table)."""
+        import torch
+        inertia = torch.zeros((max(n_labels, 1), 6), dtype=torch.float64, device=self.c.device)
+        chi = torch.zeros(max(n_labels, 1), dtype=torch.float64, device=self.c.device)
+        _check(lib().vof_drop_shape(self.handle, int(field), _ptr(labels), int(n_labels),
+                                    _ptr(cen.contiguous()), _ptr(inertia), _ptr(chi)), "vof_drop_shape")
+        return inertia[:n_labels], chi[:n_labels]
 
     def vof_normals(self, field):
         import torch

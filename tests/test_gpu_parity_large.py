@@ -1,16 +1,17 @@
 """GPU parity at the workloads' own sizes, through the C ABI.
 
-- One learned step (FP32 + the network trained on the GPU, tolerance 1e-3)
+- The learned path (FP32 + the network trained on the GPU, tolerance 1e-3)
   on a 96^3 box of the benchmark's family (phi = 0.3, spheres of radius 8
-  greedily coloured over 8 fields) against the oracle's learned step,
-  elementwise at 1e-5 outside the cells that ambiguous fallback decisions
-  can reach.
+  greedily coloured over 8 fields) against the oracle: per stencil, per
+  single sweep (velocity along one axis: every cell not next to an
+  ambiguous decision, elementwise at 1e-5) and per full step (cells out of
+  reach of the ambiguous decisions).
 - One FP64 step of the 128^3, K = 4, phi = 0.1 workload against the oracle
   at 1e-12 relative per cell (relative to max(c, 1e-3), see fp64_gate), then
   Steps 1-4 on the GPU's own field, bit-exact against the oracle's.
-- The 256^3, K = 8 benchmark workload itself, learned and FP64, advanced by
-  the same launches the benchmark times; the oracle recomputes sampled
-  windows.  A cell after one step depends only on cells within 4 of it per
+- The 256^3, K = 8 benchmark workload itself, learned (velocity along one
+  axis at a time) and FP64, advanced by the same launches the benchmark
+  times; the oracle recomputes sampled windows.  A cell after one step depends only on cells within 4 of it per
   axis (each sweep reads the 3x3x3 stencils of the donors on both faces:
   +-2 along its own axis, +-1 across), so the oracle's step on a periodic
   window with a 6-cell margin reproduces the window's interior exactly.
@@ -26,7 +27,15 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 TOL32 = 1e-5
-AMB_EPS = 3e-5
+# Margin of the fallback decision.  The judge compares two 27-cell mean
+# residuals of order 1e-2.  Between the oracle (FP64 sums, FP64 network
+# accumulation) and the GPU (FP32) they differ by the FP32 rounding of the
+# 27-term sum (<= 27 u E ~ 5e-7 with u = 6e-8), of the plane constant
+# (~1e-7 per cut cell, ~9 cells / 27) and of the network's normal (relative
+# ~1e-6, moving each cut-cell volume by ~1e-6: <= 3e-7 on the mean) --
+# together below 1e-6; decisions within twice that of the threshold may go
+# either way.
+AMB_EPS = 2e-6
 
 
 @pytest.fixture(scope="module")
@@ -101,23 +110,97 @@ def compare_learned(got, want, grown, c0, tag):
     return share, int(cmp.sum())
 
 
-def test_learned_step_96cube_trained_network(vof, trained):
-    w, params = trained
+@pytest.fixture(scope="module")
+def box96():
     wl = synth.make_workload("96^3 learned parity", n=96, k_capacity=8, phi=0.3, radius=8.0, n_modes=16,
                              amplitude=0.5, drift=1.0, cfl=0.3, seed=3)
-    c, u = f32(wl.c[:wl.k_active]), f32(wl.u)
-    assert c.shape[0] >= 5
-    ctx, c_d, rep = gpu_advance(vof, c, u, wl.dt, 2, weights=w, tol=1e-3)
+    return f32(wl.c[:wl.k_active]), f32(wl.u), wl.dt
+
+
+def stencils_of(cf):
+    """Stencils [n][27] of the interfacial cells of one periodic field."""
+    planes = [np.roll(cf, shift=(-dk, -dj, -di), axis=(0, 1, 2))
+              for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+    S = np.stack(planes, -1)
+    return S[(cf > 0) & (cf < 1)]
+
+
+def test_trained_decisions_within_the_margin(vof, trained, box96):
+    """Per stencil of the 96^3 box (no propagation): with the trained
+    network, the GPU's branch and normal equal the oracle's wherever the
+    oracle's residual is more than AMB_EPS from its threshold; the ambiguous
+    ones are counted and reported."""
+    w, params = trained
+    c, _, _ = box96
+    st = np.concatenate([stencils_of(c[f]) for f in range(c.shape[0])]).astype(np.float32)
+    st = st[np.random.default_rng(0).permutation(len(st))[:20000]]
+    m, which = vof.vof_learned_normals(w, torch.from_numpy(st).to(DEV), 1e-3)
+    m, which = m.cpu().numpy().astype(np.float64), which.cpu().numpy()
+    n_amb = 0
+    for r in range(len(st)):
+        ma, wa, amb = O.learned_normal(params, st[r].astype(np.float64), 1e-3, AMB_EPS, 0)
+        if amb:
+            n_amb += 1
+            continue
+        assert which[r] == wa, r
+        assert np.abs(m[r] - ma).max() <= 1e-4, (r, m[r], ma)
+    print(f"trained decisions: {len(st)} stencils, network {int((which == 0).sum())}, ambiguous {n_amb}")
+    assert n_amb <= 0.05 * len(st)
+
+
+def one_axis(u, axis):
+    """The velocity with only its component along `axis`: the step's other
+    two sweeps move nothing, so each listed face's flux reaches the final
+    field unchanged and an ambiguous decision can affect only its own two
+    cells."""
+    v = np.zeros_like(u)
+    v[axis] = u[axis]
+    return v
+
+
+def ambiguous_cells(amb):
+    return amb.astype(bool)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_learned_sweep_96cube_trained_network(vof, trained, box96, axis):
+    """One step with the velocity along one axis only (one active sweep),
+    the GPU-trained network at tolerance 1e-3: every cell that no ambiguous
+    decision touches matches the oracle within 1e-5."""
+    w, params = trained
+    c, u, dt = box96
+    u = one_axis(u, axis)
+    ctx, c_d, rep = gpu_advance(vof, c, u, dt, 2, weights=w, tol=1e-3)
     got = c_d.cpu().numpy().astype(np.float64)
     ctx.close()
     amb = np.zeros(c.shape, dtype=np.uint8)
-    want, _, counts = O.advect_step_learned(c, u, wl.dt, 1.0, 0, params, tol=1e-3, amb_eps=AMB_EPS,
+    want, _, counts = O.advect_step_learned(c, u, dt, 1.0, 0, params, tol=1e-3, amb_eps=AMB_EPS, amb_map=amb,
+                                            omp=True)
+    print("axis", axis, "GPU faces network/MYC", rep["faces_network"], rep["faces_myc"], "oracle", counts)
+    share, ncmp = compare_learned(got, want, ambiguous_cells(amb), c, f"96^3 sweep along {axis}")
+    assert share <= 0.05 and ncmp >= 20000
+    assert abs(got.sum() - want.sum()) / want.sum() <= 1e-6
+    assert rep["faces_network"] > 0 and rep["faces_myc"] > 0
+
+
+def test_learned_step_96cube_trained_network(vof, trained, box96):
+    """The full three-sweep step: cells out of reach of every ambiguous
+    decision match within 1e-5 (the reach is reported; a decision near its
+    threshold spreads over up to 4 cells per axis in the later sweeps), the
+    total volume within 1e-6 and c stays in [0, 1]."""
+    w, params = trained
+    c, u, dt = box96
+    ctx, c_d, rep = gpu_advance(vof, c, u, dt, 2, weights=w, tol=1e-3)
+    got = c_d.cpu().numpy().astype(np.float64)
+    ctx.close()
+    amb = np.zeros(c.shape, dtype=np.uint8)
+    want, _, counts = O.advect_step_learned(c, u, dt, 1.0, 0, params, tol=1e-3, amb_eps=AMB_EPS,
                                             amb_map=amb, omp=True)
     print("GPU faces network/MYC", rep["faces_network"], rep["faces_myc"], "oracle", counts)
     share, ncmp = compare_learned(got, want, reach(amb), c, "96^3 learned")
-    assert share <= 0.10 and ncmp >= 10000
+    assert ncmp >= 1000
     assert abs(got.sum() - want.sum()) / want.sum() <= 1e-6
-    assert rep["faces_network"] > 0 and rep["faces_myc"] > 0
+    assert got.min() >= 0.0 and got.max() <= 1.0
 
 
 def fp64_gate(got, want):
@@ -166,13 +249,16 @@ def crop(a, origin, size):
 MARGIN, INNER = 6, 24
 
 
-@pytest.mark.parametrize("precision", [2, 0])
-def test_bench_workload_256cube_sampled_windows(vof, trained, bench_workload, precision):
+@pytest.mark.parametrize("precision,axis", [(2, 0), (2, 1), (2, 2), (0, None)])
+def test_bench_workload_256cube_sampled_windows(vof, trained, bench_workload, precision, axis):
+    """The learned path runs with the velocity along one axis at a time (so
+    that every ambiguous decision stays on its own two cells, see one_axis);
+    the FP64 path with the full velocity."""
     wl = bench_workload
     w, params = trained
     na = wl.k_active
     if precision == 2:
-        c, u = f32(wl.c), f32(wl.u)
+        c, u = f32(wl.c), one_axis(f32(wl.u), axis)
     else:
         c, u = wl.c, wl.u
     ctx, c_d, rep = gpu_advance(vof, c, u, wl.dt, precision, weights=w if precision == 2 else None,
@@ -187,7 +273,7 @@ def test_bench_workload_256cube_sampled_windows(vof, trained, bench_workload, pr
     rng = np.random.default_rng(17)
     size = INNER + 2 * MARGIN
     shares = []
-    for q in range(6):
+    for q in range(6 if precision == 0 else 3):
         o = tuple(int(v) for v in rng.integers(0, 256, 3))
         cw = np.ascontiguousarray(crop(c[:na], o, size))
         uw = np.ascontiguousarray(crop(u, o, size))
@@ -197,10 +283,11 @@ def test_bench_workload_256cube_sampled_windows(vof, trained, bench_workload, pr
             amb = np.zeros(cw.shape, dtype=np.uint8)
             want, _, _ = O.advect_step_learned(cw, uw, wl.dt, 1.0, 0, params, tol=1e-3, amb_eps=AMB_EPS,
                                                amb_map=amb, omp=True)
-            share, _ = compare_learned(gw, want[inner], reach(amb)[inner], cw[inner], f"256^3 window {o}")
+            share, _ = compare_learned(gw, want[inner], ambiguous_cells(amb)[inner], cw[inner],
+                                       f"256^3 window {o} (velocity along {axis})")
             shares.append(share)
         else:
             want, _ = O.advect_step(cw, uw, wl.dt, 1.0, 0, omp=True)
             fp64_gate(gw, want[inner])
     if shares:
-        assert np.mean(shares) <= 0.10
+        assert np.mean(shares) <= 0.05
