@@ -236,6 +236,33 @@ vof_status vof_stats(vof_ctx *ctx, int32_t reset, vof_stats_out *out, double *hi
                      double *hist_rt_host);
 
 /*
+ * Curvature kappa of field `field` by height functions (Section 2.3: the
+ * surface-tension force sums gamma kappa_i grad C_i over the tracers, each
+ * curvature computed as for a single tracer).  For every interfacial cell
+ * (0 < c < 1): along the axis of the largest |component| of its MYC normal,
+ * the 3x3 columns of 7 cells centred on it give heights H = sum of c; if
+ * each column's end on the c = 1 side holds more than 1/2 and its other end
+ * less than 1/2, kappa = -[H_xx (1 + H_y^2) + H_yy (1 + H_x^2) -
+ * 2 H_xy H_x H_y] / (1 + H_x^2 + H_y^2)^(3/2) / h with centred differences
+ * (2/R for a drop of radius R), else NaN; NaN for cells that are not
+ * interfacial.  kappa_dev [nz][ny][nx] of the context's element type.
+ * Asynchronous.
+ */
+vof_status vof_curvature(vof_ctx *ctx, int32_t field, void *kappa_dev);
+
+/*
+ * Surface-tension source f = sum_i gamma kappa_i grad C_i over the active
+ * fields (Section 2.3), on the faces of the grid: f_dev [3][nz][ny][nx] of
+ * the context's element type receives at the low d-face of cell x
+ * sum_i gamma kappa_f,i (C_i(x) - C_i(x - e_d)) / h, kappa_f,i being the mean
+ * of the curvatures (vof_curvature) of the face's two cells where both have
+ * one, the one that does, or 0.  Uses the workspace's flux buffer as
+ * scratch.  VOF_ERR_ARG for a null f_dev or non-finite gamma.  Asynchronous.
+ */
+vof_status vof_surface_tension(vof_ctx *ctx, double gamma, void *f_dev);
+
+/*
+ * Drop shape (Appendix A)/*
  * Drop shape (Appendix A): the inertia tensor of each drop about its centre
  * of mass, I = integral over the drop of [(r.r) delta - r r], r = x - x_cen
  * under the minimum image, for the drop's colour density (each cell of the

@@ -137,6 +137,13 @@ def _declare(L):
     L.oracle_drop_inertia.restype = None
     L.oracle_drop_inertia.argtypes = [_dp, _ip, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, _dp,
                                       _dp, _dp]
+    L.oracle_curvature.restype = None
+    L.oracle_curvature.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, _dp]
+    L.oracle_curvature_along.restype = None
+    L.oracle_curvature_along.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _dp]
+    L.oracle_surface_tension.restype = None
+    L.oracle_surface_tension.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                         C.c_double, _dp]
     L.oracle_threads.restype = C.c_int
     L.oracle_threads.argtypes = [C.c_int]
     return L
@@ -258,6 +265,36 @@ def normals(c):
     out = np.zeros((nz, ny, nx, 3))
     lib().oracle_normals(_f64(c), nx, ny, nz, out)
     return out
+
+
+def curvature(c, h=1.0):
+    """Height-function curvature of every cell of one field (NaN where none)."""
+    nz, ny, nx = c.shape
+    out = np.zeros(c.shape)
+    lib().oracle_curvature(_f64(c), nx, ny, nz, float(h), out)
+    return out
+
+
+def curvature_along(c, axis, sign, h=1.0):
+    """Curvature with the height columns along `axis` and the c = 1 phase at
+    the -sign end, for every interfacial cell (NaN where a column misses the
+    interface)."""
+    nz, ny, nx = c.shape
+    out = np.zeros(c.shape)
+    lib().oracle_curvature_along(_f64(c), nx, ny, nz, float(h), int(axis), int(sign), out)
+    return out
+
+
+def surface_tension(c, kappa, gamma=1.0, h=1.0):
+    """f[3][nz][ny][nx] = sum_i gamma kappa_i grad C_i on the low faces."""
+    c = _f64(c)
+    if c.ndim == 3:
+        c = c[None]
+    kappa = _f64(kappa).reshape(c.shape)
+    K, nz, ny, nx = c.shape
+    f = np.zeros((3, nz, ny, nx))
+    lib().oracle_surface_tension(c, kappa, K, nx, ny, nz, float(h), float(gamma), f)
+    return f
 
 
 # --------------------------------------------------------------------------- tagging

@@ -379,7 +379,9 @@ static double cell_face_flux(const double *c, int nx, int ny, int nz, int i, int
         oracle_learned_normal(L->params, st, L->tol, L->amb_eps, 1 - L->amb_choice, m2, NULL);
         double F2 = oracle_face_flux(m2, oracle_plic_alpha(m2, cd), d, s);
         if (fabs(F2 - F) > 1e-7) {
-            uint8_t *a = L->amb_map + idx3(i, j, k, nx, ny), *b = L->amb_map + idx3(si, sj, sk, nx, ny);
+            /* the face's two cells: (i, j, k) and its low neighbour along d */
+            uint8_t *a = L->amb_map + idx3(i, j, k, nx, ny);
+            uint8_t *b = L->amb_map + idx3(wrap(i - di, nx), wrap(j - dj, ny), wrap(k - dk, nz), nx, ny);
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
@@ -518,6 +520,129 @@ void oracle_normals(const double *c, int nx, int ny, int nz, double *m_out)
                     oracle_myc(st, m);
                 }
             }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Curvature by height functions and the surface-tension source             */
+
+/*
+ * Curvature of one interfacial cell (Section 2.3: each tracer's curvature
+ * kappa_i enters the surface-tension force; computed per tracer as for a
+ * single one).  Height functions: along the axis a of the largest |component|
+ * of the cell's MYC normal (ties to the lower axis), the 3x3 columns of 7
+ * cells (offsets -3..3 along a) centred on the cell and its 8 neighbours
+ * across a hold heights H = sum of c (in cells).  Each column must contain
+ * the interface: its end on the side the normal points away from (the c = 1
+ * phase) holds more than 1/2, the other end less than 1/2; otherwise the
+ * cell has no curvature (returns NaN).  With the surface z = f(x, y) of the
+ * phase below it, the outward normal (-f_x, -f_y, 1)/sqrt(1 + |grad f|^2)
+ * has divergence
+ *   kappa = -[f_xx (1 + f_y^2) + f_yy (1 + f_x^2) - 2 f_xy f_x f_y]
+ *           / (1 + f_x^2 + f_y^2)^(3/2),
+ * positive for a drop (2/R for a sphere); f's derivatives are the centred
+ * differences of H over the 3x3 columns (cell units), divided by h for
+ * kappa in inverse length.  Reflecting a (the phase above instead) leaves
+ * H and this expression unchanged.
+ */
+static double curvature_along(const double *c, int nx, int ny, int nz, int i, int j, int k, double h, int a,
+                              int s)
+{
+    int b = a == 0 ? 1 : 0, e = a == 2 ? 1 : 2; /* the two other axes, in order */
+    double H[3][3];
+    for (int p = -1; p <= 1; ++p)
+        for (int q = -1; q <= 1; ++q) {
+            double sum = 0.0, lo = 0.0, hi = 0.0;
+            for (int t = -3; t <= 3; ++t) {
+                int o[3];
+                o[a] = t;
+                o[b] = p;
+                o[e] = q;
+                double v = c[idx3(wrap(i + o[0], nx), wrap(j + o[1], ny), wrap(k + o[2], nz), nx, ny)];
+                sum += v;
+                if (t == -3 * s)
+                    lo = v; /* the c = 1 end */
+                if (t == 3 * s)
+                    hi = v; /* the c = 0 end */
+            }
+            if (!(lo > 0.5 && hi < 0.5))
+                return NAN;
+            H[p + 1][q + 1] = sum;
+        }
+    double fx = 0.5 * (H[2][1] - H[0][1]), fy = 0.5 * (H[1][2] - H[1][0]);
+    double fxx = H[2][1] - 2.0 * H[1][1] + H[0][1], fyy = H[1][2] - 2.0 * H[1][1] + H[1][0];
+    double fxy = 0.25 * (H[2][2] - H[2][0] - H[0][2] + H[0][0]);
+    double g2 = 1.0 + fx * fx + fy * fy;
+    return -(fxx * (1.0 + fy * fy) + fyy * (1.0 + fx * fx) - 2.0 * fxy * fx * fy) / (g2 * sqrt(g2)) / h;
+}
+
+static double cell_curvature(const double *c, int nx, int ny, int nz, int i, int j, int k, double h)
+{
+    double st[27], m[3];
+    gather_stencil(c, nx, ny, nz, i, j, k, st);
+    oracle_myc(st, m);
+    int a = 0;
+    for (int q = 1; q < 3; ++q)
+        if (fabs(m[q]) > fabs(m[a]))
+            a = q;
+    /* the normal points to +s along a */
+    return curvature_along(c, nx, ny, nz, i, j, k, h, a, m[a] < 0.0 ? -1 : 1);
+}
+
+void oracle_curvature_along(const double *c, int nx, int ny, int nz, double h, int axis, int sign,
+                            double *kappa)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t x = idx3(i, j, k, nx, ny);
+                kappa[x] = (c[x] > 0.0 && c[x] < 1.0)
+                               ? curvature_along(c, nx, ny, nz, i, j, k, h, axis, sign < 0 ? -1 : 1)
+                               : NAN;
+            }
+}
+
+void oracle_curvature(const double *c, int nx, int ny, int nz, double h, double *kappa)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t x = idx3(i, j, k, nx, ny);
+                kappa[x] = (c[x] > 0.0 && c[x] < 1.0) ? cell_curvature(c, nx, ny, nz, i, j, k, h) : NAN;
+            }
+}
+
+/*
+ * Surface-tension source f = sum_i gamma kappa_i grad C_i (Section 2.3) on
+ * the faces of the grid: f_d at the low d-face of cell x, between x - e_d and
+ * x, is sum_i gamma kappa_f,i (C_i(x) - C_i(x - e_d)) / h with kappa_f,i the
+ * mean of the curvatures of the two cells that have one (the one of them
+ * that does; 0 if neither).  c, kappa: [K][nz][ny][nx]; f: [3][nz][ny][nx].
+ */
+void oracle_surface_tension(const double *c, const double *kappa, int K, int nx, int ny, int nz,
+                            double h, double gamma, double *f)
+{
+    int64_t N = (int64_t)nx * ny * nz;
+    for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int64_t x = idx3(i, j, k, nx, ny);
+                    int64_t xl = idx3(d == 0 ? wrap(i - 1, nx) : i, d == 1 ? wrap(j - 1, ny) : j,
+                                      d == 2 ? wrap(k - 1, nz) : k, nx, ny);
+                    double acc = 0.0;
+                    for (int q = 0; q < K; ++q) {
+                        double kl = kappa[q * N + xl], kr = kappa[q * N + x];
+                        double kf = 0.0;
+                        if (isfinite(kl) && isfinite(kr))
+                            kf = 0.5 * (kl + kr);
+                        else if (isfinite(kl))
+                            kf = kl;
+                        else if (isfinite(kr))
+                            kf = kr;
+                        acc += gamma * kf * (c[q * N + x] - c[q * N + xl]) / h;
+                    }
+                    f[d * N + x] = acc;
+                }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -55,7 +55,23 @@ int oracle_advect_step(double *c, const double *u, int nx, int ny, int nz,
  * cells with c <= 0 or c >= 1). */
 void oracle_normals(const double *c, int nx, int ny, int nz, double *m_out);
 
-/* Connected-component labels of {c > tau}, periodic, connectivity 6 or 26,
+/* Curvature of every cell of one field by height functions (Section 2.3,
+ * kappa_i of each tracer): NaN where the cell is not interfacial or its 3x3
+ * columns of 7 cells along the dominant MYC axis do not all contain the
+ * interface; positive for a drop (2/R for a sphere of radius R). */
+void oracle_curvature(const double *c, int nx, int ny, int nz, double h, double *kappa);
+/* The same with the height axis and the side of the c = 1 phase given
+ * (columns along `axis`, the phase at the -sign end) for every cell. */
+void oracle_curvature_along(const double *c, int nx, int ny, int nz, double h, int axis, int sign,
+                            double *kappa);
+
+/* Surface-tension source f = sum_i gamma kappa_i grad C_i on the low
+ * d-faces ([3][nz][ny][nx]) from c and kappa ([K][nz][ny][nx]); the face
+ * curvature is the mean of the two cells' where both have one. */
+void oracle_surface_tension(const double *c, const double *kappa, int K, int nx, int ny, int nz,
+                            double h, double gamma, double *f);
+
+/* Connected-component labels of {c > tau}/* Connected-component labels of {c > tau}, periodic, connectivity 6 or 26,
  * numbered 1..n in the order of each component's smallest linear index.
  * Returns n, or -1 on allocation failure. */
 int64_t oracle_label(const double *c, int nx, int ny, int nz, double tau,

@@ -844,6 +844,39 @@ vof_status vof_stats(vof_ctx* ctx, int32_t reset, vof_stats_out* out, double* hi
     return VOF_OK;
 }
 
+vof_status vof_curvature(vof_ctx* ctx, int32_t field, void* kappa_dev) {
+    vof_status s = check_ctx(ctx);
+    if (s != VOF_OK) return s;
+    if (field < 0 || field >= ctx->cfg.k_capacity || !kappa_dev) return VOF_ERR_ARG;
+    const char* cf = (const char*)ctx->c + (size_t)field * ctx->g.N * ctx->es;
+    VOF_CUDA(ctx, timed(ctx, P_MISC, [&] {
+        return curvature_field(ctx->fp64, cf, ctx->g, ctx->cfg.h, kappa_dev, ctx->stream);
+    }));
+    ctx->launches += 1;
+    return VOF_OK;
+}
+
+vof_status vof_surface_tension(vof_ctx* ctx, double gamma, void* f_dev) {
+    vof_status s = check_ctx(ctx);
+    if (s != VOF_OK) return s;
+    if (!f_dev || !std::isfinite(gamma)) return VOF_ERR_ARG;
+    const Dims& g = ctx->g;
+    // the flux buffer ([K][N], the state's element type) is free between
+    // calls: it holds the curvature of every active field here
+    char* kap = ctx->slot<char>(S_FLUX);
+    for (int f = 0; f < ctx->n_active; ++f) {
+        const char* cf = (const char*)ctx->c + (size_t)f * g.N * ctx->es;
+        VOF_CUDA(ctx, timed(ctx, P_MISC, [&] {
+            return curvature_field(ctx->fp64, cf, g, ctx->cfg.h, kap + (size_t)f * g.N * ctx->es, ctx->stream);
+        }));
+    }
+    VOF_CUDA(ctx, timed(ctx, P_MISC, [&] {
+        return surface_tension(ctx->fp64, ctx->c, kap, ctx->n_active, g, ctx->cfg.h, gamma, f_dev, ctx->stream);
+    }));
+    ctx->launches += ctx->n_active + 1;
+    return VOF_OK;
+}
+
 vof_status vof_drop_shape(vof_ctx* ctx, int32_t field, const int32_t* label_dev, int32_t n_labels,
                           const double* cen_dev, double* inertia_dev, double* chi_dev) {
     vof_status s = check_ctx(ctx);

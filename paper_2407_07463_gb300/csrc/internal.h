@@ -140,6 +140,12 @@ cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* 
                       double* S, int n_max, cudaStream_t st);
 cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, double h, int n,
                           double* vol, double* cen, cudaStream_t st);
+// Height-function curvature of one field (NaN where a cell has none) and
+// the surface-tension source f[3][N] = sum over K fields of gamma kappa grad c
+// on the low faces (Section 2.3).
+cudaError_t curvature_field(bool fp64, const void* cf, const Dims& g, double h, void* kappa, cudaStream_t st);
+cudaError_t surface_tension(bool fp64, const void* c, const void* kappa, int K, const Dims& g, double h,
+                            double gamma, void* f, cudaStream_t st);
 // Drop shape (Appendix A): I[n][6] = xx yy zz xy xz yz about cen (cleared
 // first), then chi = sqrt(I_max / I_min) per drop (chi may be null) with
 // acc[0] += sum chi, acc[1] += drops, acc[2] = max(acc[2], chi) (acc may be

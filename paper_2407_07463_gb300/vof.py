@@ -106,7 +106,8 @@ EXPORTS = ["vof_config_default", "vof_workspace_size", "vof_init", "vof_set_velo
            "vof_mlp_params_to_weights", "vof_set_mlp", "vof_learned_normals",
            "vof_batch_config_default", "vof_batch_workspace_size", "vof_batch_init", "vof_batch_set_mlp",
            "vof_batch_tune", "vof_batch_step", "vof_batch_report", "vof_batch_destroy",
-           "vof_last_cuda_error", "vof_wait_selftest", "vof_drop_shape"]
+           "vof_last_cuda_error", "vof_wait_selftest", "vof_drop_shape", "vof_curvature",
+           "vof_surface_tension"]
 
 
 def lib():
@@ -131,6 +132,8 @@ def lib():
         "vof_stats": (C.c_int, [vp, i32, C.POINTER(vof_stats_out), vp, vp]),
         "vof_drop_table": (C.c_int, [vp, i32, vp, i32, vp, vp]),
         "vof_drop_shape": (C.c_int, [vp, i32, vp, i32, vp, vp, vp]),
+        "vof_curvature": (C.c_int, [vp, i32, vp]),
+        "vof_surface_tension": (C.c_int, [vp, dbl, vp]),
         "vof_pair_stats": (C.c_int, [vp, i64, vp, i32, i32, dbl, i32, dbl, dbl, vp, vp, vp, vp]),
         "vof_plic_volume": (C.c_int, [i32, vp, vp, vp, i64, vp]),
         "vof_plic_alpha": (C.c_int, [i32, vp, vp, vp, i64, dbl, vp]),
@@ -484,6 +487,23 @@ class Context:
         _check(lib().vof_drop_shape(self.handle, int(field), _ptr(labels), int(n_labels),
                                     _ptr(cen.contiguous()), _ptr(inertia), _ptr(chi)), "vof_drop_shape")
         return inertia[:n_labels], chi[:n_labels]
+
+    def vof_curvature(self, field, out=None):
+        """Height-function curvature of one field (NaN where a cell has none)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.cfg.nz, self.cfg.ny, self.cfg.nx), dtype=self.c.dtype, device=self.c.device)
+        _check(lib().vof_curvature(self.handle, int(field), _ptr(out)), "vof_curvature")
+        return out
+
+    def vof_surface_tension(self, gamma, out=None):
+        """f[3][nz][ny][nx] = sum_i gamma kappa_i grad C_i on the low faces."""
+        import torch
+        if out is None:
+            out = torch.empty((3, self.cfg.nz, self.cfg.ny, self.cfg.nx), dtype=self.c.dtype,
+                              device=self.c.device)
+        _check(lib().vof_surface_tension(self.handle, float(gamma), _ptr(out)), "vof_surface_tension")
+        return out
 
     def vof_normals(self, field):
         import torch

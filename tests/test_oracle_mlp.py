@@ -178,3 +178,24 @@ def test_pair_inputs_within_their_error_bound_of_fp64_inputs(oracle):
         hi_only = W3 @ g2 + p[7296:7299]
         assert np.abs(hi_only - exact).max() > 20 * np.abs(pair - exact).max(), trial
     print("largest share of the bound used by the pair forward:", worst)
+
+
+def test_ambiguity_map_marks_both_cells_of_a_face(oracle):
+    """With every decision ambiguous, each face whose two branches give
+    different fluxes marks both cells it separates, whichever way the
+    velocity points: along x, under a uniform velocity of either sign, no
+    marked cell is without a marked neighbour along x."""
+    from helpers import youngs_network
+    from paper_2407_07463_gb300 import synth
+    shape = (12, 14, 16)
+    c = synth.sphere_cell_fractions(shape, np.array([[8.3, 7.1, 6.2]]), 4.0)[None]
+    p = youngs_network(0.05, seed=4)
+    for sgn in (1.0, -1.0):
+        u = np.zeros((3,) + shape)
+        u[0] = 0.8 * sgn
+        amb = np.zeros(c.shape, dtype=np.uint8)
+        oracle.advect_step_learned(c, u, 0.25, 1.0, 0, p, tol=0.0, amb_eps=1e9, amb_map=amb)
+        m = amb[0].astype(bool)
+        assert m.sum() > 20
+        paired = m & (np.roll(m, 1, axis=2) | np.roll(m, -1, axis=2))
+        assert np.array_equal(paired, m), sgn
