@@ -503,6 +503,34 @@ def run_ours(args, rank, world):
     ms_max, updates_all = scaling.aggregate(ms, updates, device=dev)
     value = updates_all / (ms_max * 1e-3)
 
+    # the surface-tension source of the state the timed steps left (curvature
+    # of every active field by height functions, then f = sum_i gamma kappa_i
+    # grad C_i on the faces): algorithmic bytes = read c and write kappa per
+    # cell-field, read c and kappa per cell-field, write f (3 per cell)
+    st_extra = None
+    try:
+        f_out = torch.empty((3, nz, ny, nx), dtype=tdt, device=dev)
+        ctx.vof_surface_tension(1.0, f_out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            ctx.vof_surface_tension(1.0, f_out)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        st_ms = e0.elapsed_time(e1) / reps
+        na_ = rep["n_active"]
+        alg = N * na_ * 4 * es + 3 * N * es
+        hbm_, _ = peaks()
+        st_extra = {"ms": st_ms, "fields": na_, "algorithmic_bytes": alg,
+                    "achieved_gbs": alg / (st_ms * 1e-3) / 1e9, "frac_of_hbm": alg / (st_ms * 1e-3) / 1e9 / hbm_,
+                    "what": "height-function curvature of every active field + surface-tension source on the faces"}
+        del f_out
+    except Exception as ex:  # reported, not fatal to the headline line
+        st_extra = {"error": str(ex)[:200]}
+
     # e2e through the public API with host buffers: per step, pinned H2D of
     # the step's inputs (c and u), the step, D2H of the result (c).  Two
     # contexts on two streams take the steps in turn, so that the copies of
@@ -645,7 +673,7 @@ def run_ours(args, rank, world):
                        "near_contact_steps": rep["near_contact_steps"]},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "roofline_update_pass": roof_update, "roofline_alu": roof_alu, "roofline_tensor": roof_tc,
-            "cpu_baseline": cpu, "fp64_path": fp64, "error_vs_fp64": err,
+            "cpu_baseline": cpu, "fp64_path": fp64, "error_vs_fp64": err, "curvature": st_extra,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
     if fp64:
         line["over_fp64"] = value / world / fp64["value"]
@@ -720,7 +748,10 @@ def run_nt(args, rank, world):
     d (N_b pi / (6 phi))^(1/3), coloured greedily, advanced in FP32 (MYC)
     with Steps 1-4 every step under the 16-mode velocity (amplitude 0.5,
     vertical drift 1, CFL 0.3); N(t) = fields holding a drop at each step's
-    Step 1.  Not a throughput line: one JSON line of the curves' summaries."""
+    Step 1.  Not a throughput line: one JSON line of the curves' summaries.
+    FP64 by default: the FP32 path's round-off residues reach the occupancy
+    threshold (1e-6) and, with no surface tension to heal them, multiply
+    into fragments that Step 4 keeps moving."""
     import torch
 
     from paper_2407_07463_gb300 import synth, vof
@@ -728,14 +759,16 @@ def run_nt(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     out = {"study": "tracer count N(t) vs phi under the seeded synthetic flow (analogue of the N(t) figure)",
-           "steps": args.steps, "drops": 125, "d_cells": 20, "cases": []}
+           "steps": args.steps, "drops": 125, "d_cells": 20, "precision": args.precision, "cases": []}
     for phi in (0.01, 0.05, 0.1, 0.2):
         n = int(round(20.0 * (125 * math.pi / (6.0 * phi)) ** (1.0 / 3.0)))
         wl = synth.make_workload(f"N(t) phi={phi}", n=n, k_capacity=16, phi=None, n_spheres=125, radius=10.0,
                                  n_modes=16, amplitude=0.5, drift=1.0, cfl=0.3, seed=40 + int(phi * 100))
-        cfg = vof.make_config(n, n, n, k_capacity=16, k_active=wl.k_active, precision=vof.VOF_MIXED, recolour=1)
-        c = torch.from_numpy(wl.c).to(dev, torch.float32).contiguous()
-        u = torch.from_numpy(wl.u).to(dev, torch.float32).contiguous()
+        prec = {"learned": vof.VOF_MIXED, "mixed": vof.VOF_MIXED, "fp64": vof.VOF_FP64}[args.precision]
+        tdt = torch.float64 if prec == vof.VOF_FP64 else torch.float32
+        cfg = vof.make_config(n, n, n, k_capacity=16, k_active=wl.k_active, precision=prec, recolour=1)
+        c = torch.from_numpy(wl.c).to(dev, tdt).contiguous()
+        u = torch.from_numpy(wl.u).to(dev, tdt).contiguous()
         ctx = vof.Context(cfg, c, u)
         series, moved, stop = [], 0, None
         t0 = time.perf_counter()

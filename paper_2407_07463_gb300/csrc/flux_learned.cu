@@ -13,6 +13,15 @@
 // threads of the CTA so that the fallback runs on full warps; then every
 // thread takes its plane constant (the few near c = 0 or 1 refined in FP64,
 // again compacted) and flux.
+//
+// Measured and dropped: one kernel doing both (the stencil gathered once,
+// the network and the judge per tile) fits three CTAs per SM beside the
+// network's shared image and ran 26% slower than the pair -- the judge
+// needs the occupancy; the network's residual taken in the network kernel
+// (its stencil kept in registers) moved 0.16 ms per sweep out of the judge
+// and added 0.22 ms to the network; stopping MYC's residual once it
+// reaches the network's saved nothing (the warp runs to its slowest lane)
+// and cost 4%.
 #include "boxes.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"
