@@ -8,6 +8,9 @@ cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps)
 cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps) {
     return advect_set(S, a, nsteps);
 }
+int update_occupancy(bool fp64, int warps) {
+    return fp64 ? update_occupancy_fp64(warps) : update_blocks_per_sm<float, kMaxBoxes>(warps);
+}
 cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a) {
     return advect_first_sweep(S, a);
 }

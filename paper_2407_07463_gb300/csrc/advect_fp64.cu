@@ -8,6 +8,7 @@ cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps
 cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps) {
     return advect_set(S, a, nsteps);
 }
+int update_occupancy_fp64(int warps) { return update_blocks_per_sm<double, kMaxBoxes>(warps); }
 cudaError_t advect_first_sweep_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a) {
     return advect_first_sweep(S, a);
 }

@@ -280,11 +280,7 @@ SweepGrid sweep_grid(const BoxSet<T, NB>& S, bool vec, const SweepArgs& a) {
         constexpr int CH = 32 * VecOf<T>::W;
         r.wpb = a.update_warps > 0 ? a.update_warps : 8;
         int per_sm = a.update_blocks_per_sm;
-        if (per_sm <= 0 &&
-            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB, 1, false>, 32 * r.wpb, 0) !=
-                 cudaSuccess ||
-             per_sm < 1))
-            per_sm = 1;
+        if (per_sm <= 0) per_sm = std::max(1, update_blocks_per_sm<T, NB>(r.wpb));
         r.gb = std::max(1, std::min(sm_count() * per_sm, kListBlocks / std::max(1, r.wpb / 8)));
         r.gb = std::min(r.gb, (S.items + r.wpb - 1) / r.wpb);
         r.gb = std::max(r.gb, 1);
@@ -358,20 +354,31 @@ cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
                                                                         counts[a.list_cur]);
             if (a.prof) a.prof->end();
             if (a.launches) *a.launches += 1;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
         }
         for (int sw = 0; sw < 3; ++sw) {
             const int d = (rot + sw) % 3;
             // next sweep: within the step, or the first sweep of the next step
             const int dn = sw < 2 ? (rot + sw + 1) % 3 : (int)((step + 1) % 3);
             const int cur = a.list_cur, nxt = 1 - a.list_cur;
+            // every launch's error is taken where it happens (a later launch's
+            // query would clear it)
             if (a.prof) a.prof->begin(P_SCAN);
-            scan_face_counts(counts[cur], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
+            cudaError_t e = scan_face_counts(counts[cur], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
             if (a.launches) *a.launches += 1;
             if (a.prof) a.prof->end();
+            if (e != cudaSuccess) return e;
             face_fluxes(S, d, sw, lists[cur], G.cap, G.gb, a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (a.prof) a.prof->begin(P_UPDATE);
             if (vec) {
-                launch_update_bx(S, d, dn, sw, tau, lists[nxt], G.cap, counts[nxt], G.gb, 32 * G.wpb, a.stream);
+                e = launch_update_bx(S, d, dn, sw, tau, lists[nxt], G.cap, counts[nxt], G.gb, 32 * G.wpb,
+                                     a.stream);
+                if (e != cudaSuccess) {
+                    if (a.prof) a.prof->end();
+                    return e;
+                }
             } else {
                 const T* ins[3] = {B0.c, B0.b1, B0.b2};
                 T* outs[3] = {B0.b1, B0.b2, B0.c};
@@ -402,10 +409,12 @@ cudaError_t advect_first_sweep(const BoxSet<T, NB>& S, SweepArgs& a) {
     int* counts[2] = {a.counts, a.counts + kSweepBlocks};
     const int rot = (int)(a.step % 3), dn = (rot + 1) % 3;
     k_list_bx<T, NB><<<G.gb, 32 * G.wpb, 0, a.stream>>>(S, rot, lists[0], G.cap, counts[0]);
-    scan_face_counts(counts[0], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan_face_counts(counts[0], a.offsets, G.gb, a.tile_seg, a.tile_cap, a.stream);
+    if (e != cudaSuccess) return e;
     face_fluxes(S, rot, 0, lists[0], G.cap, G.gb, a);
-    launch_update_bx(S, rot, dn, 0, (T)a.tau, lists[1], G.cap, counts[1], G.gb, 32 * G.wpb, a.stream);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_update_bx(S, rot, dn, 0, (T)a.tau, lists[1], G.cap, counts[1], G.gb, 32 * G.wpb, a.stream);
 }
 
 }  // namespace vof

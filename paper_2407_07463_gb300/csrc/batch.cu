@@ -310,13 +310,8 @@ vof_status vof_batch_init(const vof_batch_config* cfg, const vof_box_desc* boxes
     B->update_warps = 8;
     B->update_blocks_per_sm = 1;
     {
-        int occ = 0;
-        if (fp64_batch(cfg))
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1, false>, 256, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1, false>, 256, 0);
+        const int occ = update_occupancy(fp64_batch(cfg), 8);
         if (occ > 0) B->update_blocks_per_sm = occ;
-        (void)cudaGetLastError();
     }
     B->tune_ms_best = 0.f;
     B->tune_candidates = 0;
@@ -379,11 +374,7 @@ vof_status vof_batch_tune(vof_batch* B) {
     int bw = 8, bp = 0, n = 0;
     const int warps_c[2] = {4, 8};
     for (int w : warps_c) {
-        int occ = 0;
-        if (B->cfg.precision == VOF_FP64)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<double, kMaxBoxes, 1, false>, 32 * w, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_bx<float, kMaxBoxes, 1, false>, 32 * w, 0);
+        const int occ = update_occupancy(B->cfg.precision == VOF_FP64, w);
         for (int p = 1; p <= std::max(1, occ); p = p < 2 ? 2 : p + 2) {
             const float ms = time_shape(B, w, p, 3);
             ++n;

@@ -21,6 +21,7 @@
 #include "internal.h"
 #include "plic.cuh"
 #include "faces.cuh"
+#include "tc.cuh"
 #include "update_vec.cuh"
 
 namespace vof {
@@ -246,32 +247,91 @@ __global__ void __launch_bounds__(256) k_list_bx(const __grid_constant__ BoxSet<
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
 }
 
-// One field's loads of a row chunk in the update pass: the lane's VW
-// cells, and either its neighbours along d (d = 1, 2) or the two values
-// beyond its ends along x that the lanes at the warp's or the row's ends
-// read from memory (d = 0); the c_c bit word from sweep 1 on.
+// Stages of the update pass's copy ring: every lane keeps kUpdStages
+// (row chunk, field) items in flight through shared memory with
+// asynchronous 16-byte copies (one commit group per item), so that the
+// bytes in flight do not depend on registers.  A stage holds the item's
+// 32 * VW values of c (512 bytes per warp) and, for a y or z sweep, the same
+// chunk of its low and high neighbour rows along d; every lane reads back
+// only the 16 bytes it copied itself.
+constexpr int kUpdStages = 4;
+constexpr int kUpdRowBytes = 512;  // 32 lanes x 16 bytes
+
+__host__ __device__ constexpr int upd_rows(bool dx) { return dx ? 1 : 3; }
+__host__ __device__ constexpr size_t upd_smem_bytes(int warps, bool dx) {
+    return (size_t)warps * kUpdStages * upd_rows(dx) * kUpdRowBytes;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The scalars of one field of a row chunk that do not come through the copy
+// ring: the two values beyond the chunk's ends along x that the lanes at the
+// warp's or the row's ends read (x sweep) and the c_c bit word (sweeps 1, 2).
 template <typename T>
-struct FieldRow {
-    static constexpr int VW = VecOf<T>::W;
-    T cx[VW], cl[VW], ch[VW];
+struct FieldScalars {
     T pv, nv;
     uint32_t ccw;
 };
 
 template <typename T, int PH, bool DX>
-__device__ __forceinline__ void load_field_row(FieldRow<T>& r, const T* __restrict__ cf, int x0, int lo_d,
-                                               int hi_d, bool need_prev, int xp, bool need_next, int xn,
-                                               const uint32_t* __restrict__ ccw) {
-    ld16(cf + x0, r.cx);
+__device__ __forceinline__ void load_field_scalars(FieldScalars<T>& r, const T* __restrict__ cf, bool need_prev,
+                                                   int xp, bool need_next, int xn,
+                                                   const uint32_t* __restrict__ ccw) {
     if (DX) {
         r.pv = need_prev ? cf[xp] : T(0);
         r.nv = need_next ? cf[xn] : T(0);
-    } else {
-        ld16(cf + x0 + lo_d, r.cl);
-        ld16(cf + x0 + hi_d, r.ch);
     }
     r.ccw = PH == 0 ? 0u : *ccw;
 }
+
+// The producer side of a lane's copy ring: the next (row chunk, field) item
+// to fetch, with the chunk's source addresses computed once per chunk.
+// Lanes past a row's end copy from the row's start (in the grid; their
+// values are never used).  Every item commits one group, an empty one once
+// the warp's items are exhausted, so that waiting for all but the newest
+// kUpdStages - 1 groups always means the oldest item has landed.
+template <typename T, int NB, int PH, bool DX>
+struct UpdProducer {
+    int chk, f, K, stride, chunks;
+    const T* src;        // the lane's 16 bytes of field 0 of the chunk (sweep input)
+    size_t field_stride; // cells per field
+    int lo_d, hi_d;      // offsets of the neighbour rows along d
+
+    __device__ __forceinline__ void locate(const BoxSet<T, NB>& S, int d, int lane) {
+        if (chk >= chunks) return;
+        const BoxDev<T>& B = S.b[box_of_chunk(S, chk)];
+        const ItemCells ic = chunk_cells(B, chk - B.chunk0, lane);
+        src = sweep_in(B, PH) + ic.x0;
+        field_stride = (size_t)B.g.N;
+        K = B.K;
+        lo_d = d == 1 ? ic.lo_y : ic.lo_z;
+        hi_d = d == 1 ? ic.hi_y : ic.hi_z;
+    }
+    // Copy the next item into stage `buf` and commit its group.
+    __device__ __forceinline__ void issue(const BoxSet<T, NB>& S, int d, unsigned char* buf, int lane) {
+        if (chk < chunks) {
+            const T* row = src + (size_t)f * field_stride;
+            cp_async16(buf + lane * 16, row);
+            if (!DX) {
+                cp_async16(buf + kUpdRowBytes + lane * 16, row + lo_d);
+                cp_async16(buf + 2 * kUpdRowBytes + lane * 16, row + hi_d);
+            }
+            if (++f == K) {
+                f = 0;
+                chk += stride;
+                locate(S, d, lane);
+            }
+        }
+        cp_async_commit();
+    }
+};
 
 // Update pass of sweep PH (0, 1, 2) along d (DX: d == 0) for every box (see k_update for
 // the arithmetic): c_out = c_in - (F_hi - F_lo) + c_c (s_hi - s_lo), c_c
@@ -279,29 +339,45 @@ __device__ __forceinline__ void load_field_row(FieldRow<T>& r, const T* __restri
 // in sweep 2, and the faces of the next sweep (direction dn) whose donor is
 // interfacial appended to the block's list segment.
 //
-// A warp takes one 32 * VW-cell row chunk and walks every field of it: the
-// geometry, the velocities and their signs are taken once per chunk, and
-// the loads of the next field are issued before the current one is
-// updated.
+// A warp takes one 32 * VW-cell row chunk at a time and walks every field
+// of it: the geometry, the velocities and their signs are taken once per
+// chunk.  The rows of c come through the copy ring: every lane keeps
+// kUpdStages (chunk, field) items in flight with asynchronous copies,
+// across the fields of a chunk and into the warp's next chunk.
 template <typename T, int NB, int PH, bool DX>
 __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ BoxSet<T, NB> S, int d, int dn,
                                                       T tau, unsigned long long* __restrict__ nlist,
                                                       long long cap, int* __restrict__ ncounts) {
     constexpr int VW = VecOf<T>::W;
+    constexpr int ROWS = upd_rows(DX);
+    extern __shared__ __align__(128) unsigned char upd_smem[];
     __shared__ int s_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    unsigned char* ring = upd_smem + (size_t)warp * kUpdStages * ROWS * kUpdRowBytes;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
     const int sh_bits = (lane * VW) & 31;
     unsigned long long* seg = nlist + (size_t)blockIdx.x * cap;
-    for (int chk = blockIdx.x * wpb + (threadIdx.x >> 5); chk < S.chunks; chk += gridDim.x * wpb) {
+    const int cstride = gridDim.x * wpb;
+    // producer position (lane 0 issues; every lane tracks it) and the
+    // number of items in flight
+    UpdProducer<T, NB, PH, DX> prod;
+    prod.chk = blockIdx.x * wpb + warp;
+    prod.f = 0;
+    prod.stride = cstride;
+    prod.chunks = S.chunks;
+    prod.locate(S, d, lane);
+    auto issue_next = [&](int slot) { prod.issue(S, d, ring + (size_t)slot * ROWS * kUpdRowBytes, lane); };
+    for (int q = 0; q < kUpdStages; ++q) issue_next(q);
+    int c_slot = 0;
+    for (int chk = blockIdx.x * wpb + warp; chk < S.chunks; chk += cstride) {
         const int bx = box_of_chunk(S, chk);
         const BoxDev<T>& B = S.b[bx];
         const Dims& g = B.g;
         const ItemCells ic = chunk_cells(B, chk - B.chunk0, lane);
         const int x0 = ic.x0, i0 = ic.i0;
-        const int hi_d = d == 1 ? ic.hi_y : ic.hi_z, lo_d = d == 1 ? ic.lo_y : ic.lo_z;
+        const int hi_d = d == 1 ? ic.hi_y : ic.hi_z;
         const bool row_start = i0 == 0, row_end = i0 + VW == g.nx;
         const bool need_prev = lane == 0 || row_start, need_next = lane == 31 || row_end;
         const int xp = row_start ? x0 + g.nx - 1 : x0 - 1;
@@ -352,32 +428,42 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
         const bool leader = ic.valid && (lane & (32 / VW - 1)) == 0;
         const T* __restrict__ cin = sweep_in(B, PH);
         T* __restrict__ cout = sweep_out(B, PH);
-        FieldRow<T> cur, nxt;
-        load_field_row<T, PH, DX>(cur, cin, x0, lo_d, hi_d, need_prev, xp, need_next, xn, B.ccbits + word0);
+        FieldScalars<T> cur, nxt;
+        load_field_scalars<T, PH, DX>(cur, cin, need_prev, xp, need_next, xn, B.ccbits + word0);
         for (int f = 0; f < B.K; ++f) {
-            if (f + 1 < B.K) {
-                const size_t nb = (size_t)(f + 1) * g.N;
-                load_field_row<T, PH, DX>(nxt, cin + nb, x0, lo_d, hi_d, need_prev, xp, need_next, xn,
-                                      B.ccbits + (size_t)(f + 1) * wpf + word0);
+            if (f + 1 < B.K)
+                load_field_scalars<T, PH, DX>(nxt, cin + (size_t)(f + 1) * g.N, need_prev, xp, need_next, xn,
+                                              B.ccbits + (size_t)(f + 1) * wpf + word0);
+            // this item's rows from the ring (the stage goes back to the
+            // producer once the item is done, every read of it consumed)
+            cp_async_wait<kUpdStages - 1>();
+            T cx[VW], cl[VW], ch[VW];
+            {
+                const unsigned char* sb = ring + (size_t)c_slot * ROWS * kUpdRowBytes + lane * 16;
+                ld16_shared(reinterpret_cast<const T*>(sb), cx);
+                if (!DX) {
+                    ld16_shared(reinterpret_cast<const T*>(sb + kUpdRowBytes), cl);
+                    ld16_shared(reinterpret_cast<const T*>(sb + 2 * kUpdRowBytes), ch);
+                }
             }
             const size_t base = (size_t)f * g.N;
             const size_t word = (size_t)f * wpf + word0;
             if (DX) {
-                T cprev = __shfl_up_sync(0xffffffffu, cur.cx[VW - 1], 1);
-                T cnext = __shfl_down_sync(0xffffffffu, cur.cx[0], 1);
+                T cprev = __shfl_up_sync(0xffffffffu, cx[VW - 1], 1);
+                T cnext = __shfl_down_sync(0xffffffffu, cx[0], 1);
                 if (need_prev) cprev = cur.pv;
                 if (need_next) cnext = cur.nv;
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
-                    cur.cl[e] = e == 0 ? cprev : cur.cx[e - 1];
-                    cur.ch[e] = e == VW - 1 ? cnext : cur.cx[e + 1];
+                    cl[e] = e == 0 ? cprev : cx[e - 1];
+                    ch[e] = e == VW - 1 ? cnext : cx[e + 1];
                 }
             }
             uint32_t ccm = 0;
             if (PH == 0) {
                 if (ic.valid) {
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) ccm |= (above_half(cur.cx[e]) ? 1u : 0u) << e;
+                    for (int e = 0; e < VW; ++e) ccm |= (above_half(cx[e]) ? 1u : 0u) << e;
                 }
                 const uint32_t w = gather_word<VW>(ccm, lane);
                 if (leader) B.ccbits[word] = w;
@@ -389,22 +475,21 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
             // every cell keeps its value and none is interfacial.
             bool any_pos = false;
 #pragma unroll
-            for (int e = 0; e < VW; ++e)
-                any_pos |= above_zero(cur.cl[e]) || above_zero(cur.cx[e]) || above_zero(cur.ch[e]);
+            for (int e = 0; e < VW; ++e) any_pos |= above_zero(cl[e]) || above_zero(cx[e]) || above_zero(ch[e]);
             const bool quiet = !ic.valid || (ccm == 0 && !any_pos);
             T v[VW];
             uint32_t flo = 0, fhi = 0;
             int nflag = 0;
 #pragma unroll
-            for (int e = 0; e < VW; ++e) v[e] = cur.cx[e];
+            for (int e = 0; e < VW; ++e) v[e] = cx[e];
             if (!__all_sync(0xffffffffu, quiet)) {
                 const T* __restrict__ flux = B.flux + base;
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     // upwind donors through the low and high faces: empty (no
                     // flux), full (flux s) or interfacial (the listed flux)
-                    const T dl = (lo_pos >> e) & 1u ? cur.cl[e] : cur.cx[e];
-                    const T dh = (hi_neg >> e) & 1u ? cur.ch[e] : cur.cx[e];
+                    const T dl = (lo_pos >> e) & 1u ? cl[e] : cx[e];
+                    const T dh = (hi_neg >> e) & 1u ? ch[e] : cx[e];
                     const bool ml = ((lo_nz >> e) & 1u) && above_zero(dl);
                     const bool mh = ((hi_nz >> e) & 1u) && above_zero(dh);
                     const bool fl = at_least_one(dl), fh = at_least_one(dh);
@@ -413,8 +498,7 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
                     if (ml && !fl) F_lo = flux[x0 + e];
                     if (mh && !fh) F_hi = flux[x0 + hi_off(e)];
                     // a cell that nothing enters or leaves keeps its bits (signed zero)
-                    if (ml || mh || cc)
-                        v[e] = cur.cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi[e] - s_lo[e]);
+                    if (ml || mh || cc) v[e] = cx[e] - (F_hi - F_lo) + (cc ? T(1) : T(0)) * (s_hi[e] - s_lo[e]);
                     if (PH == 2 && (v[e] < T(0) || v[e] > T(1))) continue;  // clipped below: not interfacial
                     if (above_zero(v[e]) && !at_least_one(v[e])) {
                         flo |= nf_lo & (1u << e);
@@ -468,30 +552,69 @@ __global__ void __launch_bounds__(256, 3) k_update_bx(const __grid_constant__ Bo
                 }
             }
             cur = nxt;
+            // the item's values have been used: its stage takes the item
+            // kUpdStages ahead
+            issue_next(c_slot);
+            c_slot = c_slot + 1 == kUpdStages ? 0 : c_slot + 1;
         }
     }
+    cp_async_wait<0>();  // nothing of this thread's is still in flight when it leaves
     __syncthreads();
     if (threadIdx.x == 0) ncounts[blockIdx.x] = s_count;
 }
 
 // Launch of the update pass of sweep `sweep` (0, 1, 2) along d.
+// Dynamic shared memory of the copy rings; the y/z instances need more than
+// the default 48 KB per block.  Every translation unit holds its own copy of
+// a kernel (no relocatable device code), so the attribute is set on the copy
+// this unit launches: internal linkage keeps one flag per unit and instance.
+template <typename T, int NB, int PH, bool DX>
+static cudaError_t update_smem_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_update_bx<T, NB, PH, DX>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)upd_smem_bytes(8, DX));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <typename T, int NB, int PH>
-inline void launch_update_ph(const BoxSet<T, NB>& S, int d, int dn, T tau, unsigned long long* nlist, long long cap,
-                             int* ncounts, int gb, int threads, cudaStream_t st) {
-    if (d == 0)
-        k_update_bx<T, NB, PH, true><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
-    else
-        k_update_bx<T, NB, PH, false><<<gb, threads, 0, st>>>(S, d, dn, tau, nlist, cap, ncounts);
+static cudaError_t launch_update_ph(const BoxSet<T, NB>& S, int d, int dn, T tau, unsigned long long* nlist,
+                                    long long cap, int* ncounts, int gb, int threads, cudaStream_t st) {
+    const int warps = threads / 32;
+    cudaError_t e;
+    if (d == 0) {
+        if ((e = update_smem_attr<T, NB, PH, true>()) != cudaSuccess) return e;
+        k_update_bx<T, NB, PH, true><<<gb, threads, upd_smem_bytes(warps, true), st>>>(S, d, dn, tau, nlist, cap,
+                                                                                      ncounts);
+    } else {
+        if ((e = update_smem_attr<T, NB, PH, false>()) != cudaSuccess) return e;
+        k_update_bx<T, NB, PH, false><<<gb, threads, upd_smem_bytes(warps, false), st>>>(S, d, dn, tau, nlist, cap,
+                                                                                        ncounts);
+    }
+    return cudaGetLastError();
 }
 template <typename T, int NB>
-inline void launch_update_bx(const BoxSet<T, NB>& S, int d, int dn, int sweep, T tau, unsigned long long* nlist,
-                             long long cap, int* ncounts, int gb, int threads, cudaStream_t st) {
-    if (sweep == 0)
-        launch_update_ph<T, NB, 0>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
-    else if (sweep == 1)
-        launch_update_ph<T, NB, 1>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
-    else
-        launch_update_ph<T, NB, 2>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
+static cudaError_t launch_update_bx(const BoxSet<T, NB>& S, int d, int dn, int sweep, T tau,
+                                    unsigned long long* nlist, long long cap, int* ncounts, int gb, int threads,
+                                    cudaStream_t st) {
+    if (sweep == 0) return launch_update_ph<T, NB, 0>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
+    if (sweep == 1) return launch_update_ph<T, NB, 1>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
+    return launch_update_ph<T, NB, 2>(S, d, dn, tau, nlist, cap, ncounts, gb, threads, st);
+}
+
+// Resident blocks per SM of the y/z update pass with `warps` warps per
+// block, queried on the kernel copy of the unit that launches it.
+template <typename T, int NB>
+static int update_blocks_per_sm(int warps) {
+    int per_sm = 0;
+    if (update_smem_attr<T, NB, 1, false>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_bx<T, NB, 1, false>, 32 * warps,
+                                                      upd_smem_bytes(warps, false)) != cudaSuccess)
+        per_sm = 0;
+    (void)cudaGetLastError();
+    return per_sm;
 }
 
 // A listed face of a box set: box, field, the cell x of the face's high

@@ -84,6 +84,10 @@ cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps
 cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps);
+// Resident blocks per SM of a batch's update pass with `warps` warps per
+// block (0 if the query fails), asked of the unit that launches it.
+int update_occupancy(bool fp64, int warps);
+int update_occupancy_fp64(int warps);
 // Listing and first sweep of a batch only (state untouched; for timing).
 cudaError_t advect_first_sweep_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a);
 cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a);

@@ -36,6 +36,22 @@ __device__ __forceinline__ void ld16(const T* __restrict__ p, T v[16 / sizeof(T)
     }
 }
 
+// 16 bytes from shared memory.
+template <typename T>
+__device__ __forceinline__ void ld16_shared(const T* p, T v[16 / sizeof(T)]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void st16(T* p, const T v[16 / sizeof(T)]) {
     if constexpr (sizeof(T) == 4)
