@@ -24,6 +24,7 @@ enum Slot {
     S_CCBITS,
     S_NCMAP,
     S_MVBITS,
+    S_DIL,
     S_LABELS,
     S_PARENT,
     S_RANK,
@@ -117,8 +118,10 @@ Layout layout_for(const vof_config* c) {
     L.size[S_CCBITS] = K * words * 4;
     L.size[S_NCMAP] = K * words * 4;
     L.size[S_MVBITS] = K * words * 4;
+    // Step 4: the active fields' and the moving drops' bits dilated, plus scratch
+    L.size[S_DIL] = 3 * K * words * 4;
     L.size[S_LABELS] = K * N * 4;
-    // labelling scratch, one set per field (Step 2 tags fields side by side)
+    // labelling scratch, one set per field (Step 2 tags the flagged fields together)
     L.size[S_PARENT] = K * N * 4;
     L.size[S_RANK] = K * N * 4;
     L.size[S_BTOT] = K * (nb + 1) * 4;
@@ -153,7 +156,7 @@ Layout layout_for(const vof_config* c) {
 
 }  // namespace
 
-constexpr int kSideStreams = 4;
+static_assert(kMaxK <= kLabelSlots, "Step 2 tags every flagged field in one chain of launches");
 
 struct vof_ctx {
     vof_config cfg;
@@ -176,19 +179,6 @@ struct vof_ctx {
     Prof prof;
     const void* mlp;  // borrowed weight blob of the learned normal (VOF_MIXED_LEARNED)
     double mlp_tol;
-    // streams on which the flagged fields of Step 2 are tagged side by side
-    // (forked from and joined back to `stream` by events)
-    cudaStream_t side[kSideStreams] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
-
-    ~vof_ctx() {
-        for (cudaStream_t s : side)
-            if (s) cudaStreamDestroy(s);
-        for (cudaEvent_t e : ev_join)
-            if (e) cudaEventDestroy(e);
-        if (ev_fork) cudaEventDestroy(ev_fork);
-    }
-
     template <typename P>
     P* slot(int s) const { return (P*)(ws + L.off[s]); }
     char* misc() const { return ws + L.off[S_MISC]; }
@@ -294,31 +284,19 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     VOF_CUDA(ctx, cudaMemsetAsync(table, 0xff, (size_t)kPairCap * 8, st));
     VOF_CUDA(ctx, cudaMemsetAsync(overflow, 0, sizeof(int), st));
     VOF_CUDA(ctx, cudaMemsetAsync(counters + 1, 0, sizeof(unsigned long long), st));
-    // the flagged fields are tagged (and their pairs inserted) side by side,
-    // one labelling scratch set each, on the side streams
-    const int nfl = (int)flagged.size();
-    const int nss = std::min(nfl, kSideStreams);
-    const size_t nb = ((size_t)g.N + 1023) / 1024;
+    // the flagged fields are tagged (and their pairs inserted) together: one
+    // chain of launches whose blocks take a field each (blockIdx.y), with a
+    // labelling scratch set per flagged field
+    LabelSlots ls{};
+    ls.n = (int)flagged.size();
+    for (int i = 0; i < ls.n; ++i) ls.f[i] = flagged[i];
     VOF_CUDA(ctx, timed(ctx, P_LABEL, [&]() -> cudaError_t {
-                 cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
-                 for (int i = 0; i < nss && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->side[i], ctx->ev_fork, 0);
-                 for (int i = 0; i < nfl && e == cudaSuccess; ++i) {
-                     const int f = flagged[i];
-                     cudaStream_t ss = ctx->side[i % nss];
-                     int* lab = labels + (size_t)f * g.N;
-                     e = label_field(bits + (size_t)f * words, g, cf.connectivity,
-                                     ctx->slot<int>(S_PARENT) + (size_t)i * g.N, ctx->slot<int>(S_RANK) + (size_t)i * g.N,
-                                     ctx->slot<int>(S_BTOT) + i * (nb + 1), ctx->slot<int>(S_BOFF) + i * (nb + 1), lab,
-                                     nullptr, 0, nout + f, ss, &ctx->launches);
-                     if (e == cudaSuccess)
-                         e = tag_pairs(ncmap + (size_t)f * words, bits + (size_t)f * words, lab, g, cf.stencil_w, f,
-                                       table, kPairCap, overflow, ss);
-                     ctx->launches += 1;
-                 }
-                 for (int i = 0; i < nss && e == cudaSuccess; ++i) {
-                     e = cudaEventRecord(ctx->ev_join[i], ctx->side[i]);
-                     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join[i], 0);
-                 }
+                 cudaError_t e = label_fields(bits, g, cf.connectivity, ls, ctx->slot<int>(S_PARENT),
+                                              ctx->slot<int>(S_RANK), ctx->slot<int>(S_BTOT),
+                                              ctx->slot<int>(S_BOFF), labels, nout, st, &ctx->launches);
+                 if (e == cudaSuccess)
+                     e = tag_pairs_fields(ncmap, bits, labels, g, cf.stencil_w, ls, table, kPairCap, overflow, st);
+                 ctx->launches += 1;
                  return e;
              }));
     VOF_CUDA(ctx, timed(ctx, P_PAIRS, [&] { return compact_pairs(table, kPairCap, plist, counters + 1, st); }));
@@ -385,10 +363,10 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     VOF_CUDA(ctx, cudaMemsetAsync(touch, 0, (size_t)M * 4, st));
     VOF_CUDA(ctx, cudaMemsetAsync(conflict, 0, (size_t)M * kMoveWords * 4, st));
     VOF_CUDA(ctx, timed(ctx, P_TOUCH, [&] {
-                 return recolour_touch(labels, bits, ctx->slot<uint32_t>(S_MVBITS), g, K, na0, 2 * cf.stencil_w,
-                                       mt, d_fields, (int)hfields.size(), touch, conflict, kMoveWords, st);
+                 return recolour_touch(labels, bits, ctx->slot<uint32_t>(S_MVBITS), ctx->slot<uint32_t>(S_DIL), g,
+                                       na0, 2 * cf.stencil_w, mt, d_fields, (int)hfields.size(), touch, conflict,
+                                       kMoveWords, st, &ctx->launches);
              }));
-    ctx->launches += 1;
     std::vector<unsigned> htouch(M), hconf((size_t)M * kMoveWords);
     VOF_CUDA(ctx, cudaMemcpyAsync(htouch.data(), touch, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
     VOF_CUDA(ctx, cudaMemcpyAsync(hconf.data(), conflict, (size_t)M * kMoveWords * 4, cudaMemcpyDeviceToHost, st));
@@ -423,7 +401,8 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     int* d_target = ctx->slot<int>(S_TARGET);
     VOF_CUDA(ctx, cudaMemcpyAsync(d_target, target.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
     VOF_CUDA(ctx, timed(ctx, P_MOVE, [&] {
-                 return recolour_move(ctx->cur, ctx->fp64, labels, g, mt, d_fields, (int)hfields.size(), d_target, st);
+                 return recolour_move(ctx->cur, ctx->fp64, labels, ctx->slot<uint32_t>(S_MVBITS), g, mt, d_fields,
+                                     (int)hfields.size(), d_target, st);
              }));
     ctx->launches += 1;
     ctx->bits_valid = false;
@@ -553,15 +532,6 @@ vof_status vof_init(const vof_config* cfg, void* c_dev, const void* u_dev, void*
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_R], 0, L.size[S_HIST_R], ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_HIST_RT], 0, L.size[S_HIST_RT], ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws + L.off[S_MOM], 0, L.size[S_MOM], ctx->stream) != cudaSuccess) {
-        (void)cudaGetLastError();
-        delete ctx;
-        return VOF_ERR_CUDA;
-    }
-    bool made = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < kSideStreams && made; ++i)
-        made = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) == cudaSuccess &&
-               cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
-    if (!made) {
         (void)cudaGetLastError();
         delete ctx;
         return VOF_ERR_CUDA;

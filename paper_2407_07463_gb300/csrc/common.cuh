@@ -155,6 +155,14 @@ __device__ __forceinline__ uint32_t row_window(const uint32_t* __restrict__ row,
     return r;
 }
 
+// Bits x0 + dx .. x0 + dx + 31 from the words left, centre and right of x0
+// (|dx| < 32).
+__device__ __forceinline__ uint32_t shift_window(uint32_t l, uint32_t c, uint32_t r, int dx) {
+    if (dx == 0) return c;
+    if (dx > 0) return __funnelshift_r(c, r, dx);
+    return __funnelshift_l(l, c, -dx);
+}
+
 __device__ __forceinline__ bool bit_at(const uint32_t* __restrict__ bits, int W, int row, int i) {
     return (bits[(size_t)row * W + (i >> 5)] >> (i & 31)) & 1u;
 }

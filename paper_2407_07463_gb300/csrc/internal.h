@@ -120,8 +120,24 @@ cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, cons
 cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
                         int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
                         cudaStream_t st, long long* launches);
-cudaError_t tag_pairs(const uint32_t* ncmap_f, const uint32_t* bits_f, const int* label_f, const Dims& g,
-                      int w, int f, unsigned long long* table, int cap, int* overflow, cudaStream_t st);
+// Fields tagged by one chain of launches (slot s = blockIdx.y takes field
+// f[s]).  A field's bit plane, near-contact map and labels sit f * words and
+// f * N from their bases and its drop count at n_out[f]; a slot's scratch
+// sits s * N (parent, rank) and s * (nb + 1) (block totals and offsets, nb =
+// ceil(N / 1024)) from theirs.
+constexpr int kLabelSlots = 16;
+struct LabelSlots {
+    int n;
+    int f[kLabelSlots];
+};
+cudaError_t label_fields(const uint32_t* bits, const Dims& g, int conn, const LabelSlots& ls, int* parent, int* rank,
+                         int* block_tot, int* block_off, int* labels, int* n_out, cudaStream_t st,
+                         long long* launches);
+// Step 3 for the slots' fields: distinct pairs of the tags of opposite
+// occupied cells around every near-contact cell, into the set `table`.
+cudaError_t tag_pairs_fields(const uint32_t* ncmap, const uint32_t* bits, const int* labels, const Dims& g, int w,
+                             const LabelSlots& ls, unsigned long long* table, int cap, int* overflow,
+                             cudaStream_t st);
 cudaError_t compact_pairs(const unsigned long long* table, int cap, unsigned long long* out,
                           unsigned long long* count, cudaStream_t st);
 
@@ -133,11 +149,15 @@ struct MoveTables {
     const int* mv_label;   // [M]
     int M;
 };
-cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, const Dims& g, int K,
+// Moving-drop bits (mvbits: a plane per field of mv_fields), then touch[m]
+// and conflict[m] for every moving drop; dil: scratch of n_active +
+// 2 n_mv_fields bit planes; reach <= 16, n_active and n_mv_fields <= 32.
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, uint32_t* dil, const Dims& g,
                            int n_active, int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
-                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st);
-cudaError_t recolour_move(void* c, bool fp64, const int* labels, const Dims& g, MoveTables mt,
-                          const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);
+                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st, long long* launches);
+// Moves the cells set in mvbits to their drop's target field.
+cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t* mvbits, const Dims& g,
+                          MoveTables mt, const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);
 
 // Statistics helpers.
 cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* parent, const Dims& g,

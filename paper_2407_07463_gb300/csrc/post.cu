@@ -1,5 +1,7 @@
 // Step 4 (recolouring) kernels, drop table and nearest-particle statistics
 // (Section 2.3 Step 4; Section 3), plus the stateless PLIC primitives.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "plic.cuh"
@@ -24,28 +26,32 @@ __device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) 
 }
 
 // Occupancy bits of the cells of moving drops, one bit plane per field of
-// mv_fields (same row layout as the occupancy bits).
-__global__ void k_moving_bits(const int* __restrict__ labels, Dims g, MoveTables mt,
-                              const int* __restrict__ mv_fields, int n_mv_fields, uint32_t* __restrict__ mvbits) {
-    long long per_field = (long long)g.rows * g.W;
-    long long words = (long long)n_mv_fields * per_field;
-    int lane = threadIdx.x & 31;
-    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long wd = warp; wd < words; wd += nwarps) {
-        int q = (int)(wd / per_field);
-        long long rem = wd - (long long)q * per_field;
-        int row = (int)(rem / g.W);
-        int w = (int)(rem - (long long)row * g.W);
-        int x = w * 32 + lane;
-        int f = mv_fields[q];
-        bool v = false;
-        if (x < g.nx) {
-            int l = labels[(size_t)f * g.N + (size_t)row * g.nx + x];
-            v = l != 0 && moving_index(mt, f, l) >= 0;
+// mv_fields (same row layout as the occupancy bits).  A lane takes a word:
+// only its occupied cells (the field's occupancy bits, from which its tags
+// were made) read their tag.
+__global__ void __launch_bounds__(256) k_moving_bits(const int* __restrict__ labels,
+                                                     const uint32_t* __restrict__ bits, Dims g, MoveTables mt,
+                                                     const int* __restrict__ mv_fields, int n_mv_fields,
+                                                     uint32_t* __restrict__ mvbits) {
+    const long long per_field = (long long)g.rows * g.W;
+    const long long words = (long long)n_mv_fields * per_field;
+    for (long long wd = (long long)blockIdx.x * blockDim.x + threadIdx.x; wd < words;
+         wd += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(wd / per_field);
+        const long long rem = wd - (long long)q * per_field;
+        const int f = mv_fields[q];
+        uint32_t occ = bits[(size_t)f * per_field + rem], mv = 0u;
+        if (occ) {
+            const int row = (int)(rem / g.W), wi = (int)(rem - (long long)row * g.W);
+            const int* lab = labels + (size_t)f * g.N + (size_t)row * g.nx + wi * 32;
+            while (occ) {
+                const int b = __ffs(occ) - 1;
+                occ &= occ - 1u;
+                const int l = lab[b];
+                if (l != 0 && moving_index(mt, f, l) >= 0) mv |= 1u << b;
+            }
         }
-        unsigned m = __ballot_sync(0xffffffffu, v);
-        if (lane == 0) mvbits[wd] = m;
+        mvbits[wd] = mv;
     }
 }
 
@@ -55,18 +61,81 @@ __device__ __forceinline__ unsigned long long row_window64(const uint32_t* __res
            ((unsigned long long)row_window(row, W, nx, x0 + 32) << 32);
 }
 
+// Box dilation of bit planes (plane blockIdx.y at blockIdx.y * per-field
+// words), one axis per pass, periodic: a cell of dst is set when a cell of
+// src within `reach` of it along the pass's axis is.  The three passes give
+// the cells within Chebyshev distance `reach` of a set cell.
+__global__ void __launch_bounds__(256) k_dilate_x(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                  Dims g, int reach) {
+    const long long pf = (long long)g.rows * g.W;
+    src += (size_t)blockIdx.y * pf;
+    dst += (size_t)blockIdx.y * pf;
+    const bool aligned = (g.nx & 31) == 0;
+    const uint32_t tail = (g.nx & 31) ? (1u << (g.nx & 31)) - 1u : 0xffffffffu;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(w / g.W), wi = (int)(w - (long long)row * g.W);
+        const uint32_t* r = src + (size_t)row * g.W;
+        uint32_t acc = 0u;
+        if (aligned) {
+            const uint32_t l = r[wi == 0 ? g.W - 1 : wi - 1], c = r[wi], h = r[wi + 1 == g.W ? 0 : wi + 1];
+            if (l | c | h)
+                for (int dx = -reach; dx <= reach; ++dx) acc |= shift_window(l, c, h, dx);
+        } else {
+            for (int dx = -reach; dx <= reach; ++dx) acc |= row_window(r, g.W, g.nx, wi * 32 + dx);
+            if (wi == g.W - 1) acc &= tail;
+        }
+        dst[w] = acc;
+    }
+}
+
+// axis 1: along y, axis 2: along z
+__global__ void __launch_bounds__(256) k_dilate_rows(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                     Dims g, int reach, int axis) {
+    const long long pf = (long long)g.rows * g.W;
+    src += (size_t)blockIdx.y * pf;
+    dst += (size_t)blockIdx.y * pf;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(w / g.W), wi = (int)(w - (long long)row * g.W);
+        const int j = row % g.ny, k = row / g.ny;
+        uint32_t acc = 0u;
+        for (int dd = -reach; dd <= reach; ++dd) {
+            const int rr = axis == 1 ? k * g.ny + wrapi(j + dd, g.ny) : wrapi(k + dd, g.nz) * g.ny + j;
+            acc |= src[(size_t)rr * g.W + wi];
+        }
+        dst[w] = acc;
+    }
+}
+
+// Dilation of n planes from src into dst (tmp: n planes of scratch).
+static cudaError_t dilate_planes(const uint32_t* src, uint32_t* dst, uint32_t* tmp, int n, const Dims& g, int reach,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long pf = (long long)g.rows * g.W;
+    const dim3 grid(grid_for(pf, 256, std::max(1, sm_count() * 32 / n)), n);
+    k_dilate_x<<<grid, 256, 0, st>>>(src, dst, g, reach);
+    k_dilate_rows<<<grid, 256, 0, st>>>(dst, tmp, g, reach, 1);
+    k_dilate_rows<<<grid, 256, 0, st>>>(tmp, dst, g, reach, 2);
+    return cudaGetLastError();
+}
+
 // For every moving drop m: the fields (other than its own) with an occupied
 // cell within Chebyshev distance `reach` of a cell of m (touch[m], a field
 // mask), and the other moving drops within that distance (conflict[m], a
-// bit per moving drop).  One warp takes one 32-cell word of a moving-drop
-// bit plane at a time; the set bits of the word are grouped by drop, each
-// group is dilated along x by `reach` inside a 64-cell frame starting at
-// the word's first cell minus `reach`, and the lanes share the
-// (2 reach + 1)^2 rows of the window, reading each row of every field as a
-// 64-bit window of its occupancy bits (reach <= 16).
+// bit per moving drop).  dil_bits holds the occupancy of every active field
+// dilated by `reach`, dil_mv the moving-drop bits dilated the same way.  One
+// warp takes one 32-cell word of a moving-drop bit plane at a time and
+// groups its set bits by drop.  A group touches field n where n's dilated
+// occupancy meets it (lane n tests field n).  Conflicts are searched cell by
+// cell only in the moving fields whose dilated bits meet the group (its own
+// field always, for the field's other moving drops): the lanes share the
+// (2 reach + 1)^2 rows of the window and read each row as a 64-bit window
+// (reach <= 16) against the group dilated along x.
 __global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ labels,
-                                                     const uint32_t* __restrict__ bits,
-                                                     const uint32_t* __restrict__ mvbits, Dims g, int n_active,
+                                                     const uint32_t* __restrict__ mvbits,
+                                                     const uint32_t* __restrict__ dil_bits,
+                                                     const uint32_t* __restrict__ dil_mv, Dims g, int n_active,
                                                      int reach, MoveTables mt, const int* __restrict__ mv_fields,
                                                      int n_mv_fields, unsigned* __restrict__ touch,
                                                      unsigned* __restrict__ conflict, int Mw) {
@@ -96,6 +165,9 @@ __global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ lab
             // the moving drop of each set bit
             const bool set = (word >> lane) & 1u;
             const int m_lane = set ? moving_index(mt, f, lab[wi * 32 + lane]) : -1;
+            // this word of every dilated plane, one plane per lane
+            const uint32_t db = lane < n_active ? dil_bits[(size_t)lane * per_field + rem] : 0u;
+            const uint32_t dm = lane < n_mv_fields ? dil_mv[(size_t)lane * per_field + rem] : 0u;
             unsigned rest = __ballot_sync(0xffffffffu, set);
             while (rest) {
                 const int lead = __ffs(rest) - 1;
@@ -103,21 +175,22 @@ __global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ lab
                 const unsigned grp = __ballot_sync(0xffffffffu, set && m_lane == m);
                 rest &= ~grp;
                 if (m < 0) continue;
+                const unsigned tmask = __ballot_sync(0xffffffffu, lane != f && (db & grp) != 0u);
+                if (lane == 0 && tmask) atomicOr(touch + m, tmask);
+                const unsigned cand = __ballot_sync(0xffffffffu, lane == q || (dm & grp) != 0u);
                 // frame bit c <-> cell 32 wi - reach + c; cells within reach
                 // along x of the group's cells
                 unsigned long long dil = 0;
                 for (int s2 = 0; s2 <= 2 * reach; ++s2) dil |= (unsigned long long)grp << s2;
                 const int x0 = wi * 32 - reach;
-                unsigned tmask = 0;
                 for (int r2 = lane; r2 < nrows; r2 += 32) {
                     const int dz = r2 / span - reach, dy = r2 % span - reach;
                     const int kk = wrapi(k + dz, g.nz), jj = wrapi(j + dy, g.ny);
                     const size_t roff = (size_t)(kk * g.ny + jj) * g.W;
-                    for (int n = 0; n < n_active; ++n) {
-                        if (n == f || ((tmask >> n) & 1u)) continue;
-                        if (row_window64(bits + (size_t)n * per_field + roff, g.W, g.nx, x0) & dil) tmask |= 1u << n;
-                    }
-                    for (int q2 = 0; q2 < n_mv_fields; ++q2) {
+                    unsigned cm = cand;
+                    while (cm) {
+                        const int q2 = __ffs(cm) - 1;
+                        cm &= cm - 1u;
                         unsigned long long wv = row_window64(mvbits + (size_t)q2 * per_field + roff, g.W, g.nx, x0) & dil;
                         const int f2 = mv_fields[q2];
                         while (wv) {
@@ -133,53 +206,73 @@ __global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ lab
                         }
                     }
                 }
-                tmask = __reduce_or_sync(0xffffffffu, tmask);
-                if (lane == 0 && tmask) atomicOr(touch + m, tmask);
             }
         }
     }
 }
 
-cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, const Dims& g, int K,
+// dil: workspace of (n_active + 2 * n_mv_fields) bit planes.
+cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, uint32_t* dil, const Dims& g,
                            int n_active, int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
-                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st) {
-    long long words = (long long)n_mv_fields * g.rows * g.W;
-    k_moving_bits<<<grid_for(words * 32, 256), 256, 0, st>>>(labels, g, mt, mv_fields, n_mv_fields, mvbits);
+                           unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st, long long* launches) {
     if (reach > 16) return cudaErrorInvalidValue;  // the 64-cell frame holds 32 + 2 reach cells
-    k_touch_words<<<grid_for(words, 256), 256, 0, st>>>(labels, bits, mvbits, g, n_active, reach, mt, mv_fields,
-                                                         n_mv_fields, touch, conflict, Mw);
+    if (n_active > 32 || n_mv_fields > 32) return cudaErrorInvalidValue;  // one lane per plane
+    const long long pf = (long long)g.rows * g.W;
+    const long long words = (long long)n_mv_fields * pf;
+    uint32_t* dil_bits = dil;
+    uint32_t* dil_mv = dil + (size_t)n_active * pf;
+    uint32_t* tmp = dil_mv + (size_t)n_mv_fields * pf;
+    k_moving_bits<<<grid_for(words, 256), 256, 0, st>>>(labels, bits, g, mt, mv_fields, n_mv_fields, mvbits);
+    cudaError_t e = dilate_planes(bits, dil_bits, tmp, n_active, g, reach, st);
+    if (e == cudaSuccess) e = dilate_planes(mvbits, dil_mv, tmp, n_mv_fields, g, reach, st);
+    if (e != cudaSuccess) return e;
+    k_touch_words<<<grid_for(words, 256), 256, 0, st>>>(labels, mvbits, dil_bits, dil_mv, g, n_active, reach, mt,
+                                                         mv_fields, n_mv_fields, touch, conflict, Mw);
+    if (launches) *launches += 8;
     return cudaGetLastError();
 }
 
+// Step 4's move: every cell of a moving drop hands its c to the drop's
+// target field.  A lane takes a word of the moving-drop bits; only its set
+// cells are touched.
 template <typename T>
-__global__ void k_move(T* c, const int* __restrict__ labels, Dims g, MoveTables mt,
-                       const int* __restrict__ mv_fields, int n_mv_fields, const int* __restrict__ target) {
-    long long total = (long long)n_mv_fields * g.N;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int fi = (int)(t / g.N);
-        int x = (int)(t - (long long)fi * g.N);
-        int f = mv_fields[fi];
-        int l = labels[(size_t)f * g.N + x];
-        if (l == 0) continue;
-        int m = moving_index(mt, f, l);
-        if (m < 0) continue;
-        int tg = target[m];
-        if (tg < 0) continue;
-        T v = c[(size_t)f * g.N + x];
-        c[(size_t)tg * g.N + x] += v;
-        c[(size_t)f * g.N + x] = T(0);
+__global__ void __launch_bounds__(256) k_move(T* c, const int* __restrict__ labels,
+                                              const uint32_t* __restrict__ mvbits, Dims g, MoveTables mt,
+                                              const int* __restrict__ mv_fields, int n_mv_fields,
+                                              const int* __restrict__ target) {
+    const long long per_field = (long long)g.rows * g.W;
+    const long long words = (long long)n_mv_fields * per_field;
+    for (long long wd = (long long)blockIdx.x * blockDim.x + threadIdx.x; wd < words;
+         wd += (long long)gridDim.x * blockDim.x) {
+        uint32_t mv = mvbits[wd];
+        if (!mv) continue;
+        const int q = (int)(wd / per_field);
+        const long long rem = wd - (long long)q * per_field;
+        const int row = (int)(rem / g.W), wi = (int)(rem - (long long)row * g.W);
+        const int f = mv_fields[q];
+        const size_t x0 = (size_t)row * g.nx + wi * 32;
+        while (mv) {
+            const int b = __ffs(mv) - 1;
+            mv &= mv - 1u;
+            const size_t x = x0 + b;
+            const int m = moving_index(mt, f, labels[(size_t)f * g.N + x]);
+            const int tg = m >= 0 ? target[m] : -1;
+            if (tg < 0) continue;
+            const T v = c[(size_t)f * g.N + x];
+            c[(size_t)tg * g.N + x] += v;
+            c[(size_t)f * g.N + x] = T(0);
+        }
     }
 }
 
-cudaError_t recolour_move(void* c, bool fp64, const int* labels, const Dims& g, MoveTables mt,
-                          const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st) {
-    long long total = (long long)n_mv_fields * g.N;
+cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t* mvbits, const Dims& g,
+                          MoveTables mt, const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st) {
+    const long long words = (long long)n_mv_fields * g.rows * g.W;
     if (fp64)
-        k_move<double><<<grid_for(total, 256), 256, 0, st>>>((double*)c, labels, g, mt, mv_fields,
+        k_move<double><<<grid_for(words, 256), 256, 0, st>>>((double*)c, labels, mvbits, g, mt, mv_fields,
                                                             n_mv_fields, target);
     else
-        k_move<float><<<grid_for(total, 256), 256, 0, st>>>((float*)c, labels, g, mt, mv_fields,
+        k_move<float><<<grid_for(words, 256), 256, 0, st>>>((float*)c, labels, mvbits, g, mt, mv_fields,
                                                            n_mv_fields, target);
     return cudaGetLastError();
 }

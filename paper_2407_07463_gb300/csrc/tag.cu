@@ -8,6 +8,8 @@
 // each component's root is its smallest linear index) followed by a prefix
 // sum over the roots, which yields exactly the numbering of a flood fill in
 // linear-index order.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -51,14 +53,6 @@ cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, i
 // Step 1: near contact.  For every cell with c <= tau, is there an offset
 // delta in [-w,w]^3 \ {0} with both cells x + delta and x - delta occupied?
 // One offset per opposite pair: the first nonzero of (dz, dy, dx) positive.
-
-// Bits x0 + dx .. x0 + dx + 31 from the words left, centre and right of x0
-// (|dx| < 32).
-__device__ __forceinline__ uint32_t shift_window(uint32_t l, uint32_t c, uint32_t r, int dx) {
-    if (dx == 0) return c;
-    if (dx > 0) return __funnelshift_r(c, r, dx);
-    return __funnelshift_l(l, c, -dx);
-}
 
 __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict__ bits,
                                                       uint32_t* __restrict__ ncmap,
@@ -169,7 +163,17 @@ __device__ __forceinline__ void unite(int* parent, int a, int b) {
     }
 }
 
-__global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
+// The labelling kernels run one slot of a LabelSlots per blockIdx.y: the
+// slot's field selects the bit plane (and the labels), the slot itself the
+// scratch (parent and rank arrays, block totals and offsets).
+__device__ __forceinline__ const uint32_t* slot_bits(const uint32_t* bits, const LabelSlots& ls, const Dims& g) {
+    return bits + (size_t)ls.f[blockIdx.y] * ((size_t)g.rows * g.W);
+}
+__host__ __device__ __forceinline__ int label_blocks(const Dims& g) { return (g.N + 1023) / 1024; }
+
+__global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits, int* __restrict__ parent, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
     const long long words = (long long)g.rows * g.W;
     for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
          gw += (long long)gridDim.x * blockDim.x) {
@@ -200,7 +204,9 @@ __device__ __forceinline__ void join_rows(int* parent, uint32_t w, uint32_t wn, 
     }
 }
 
-__global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
+__global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits, int* parent, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
     const long long words = (long long)g.rows * g.W;
     for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
          gw += (long long)gridDim.x * blockDim.x) {
@@ -224,14 +230,18 @@ __global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits_f, int* paren
     }
 }
 
-__global__ void k_ccl_init(const uint32_t* __restrict__ bits_f, int* __restrict__ parent, Dims g) {
+__global__ void k_ccl_init(const uint32_t* __restrict__ bits, int* __restrict__ parent, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
         int i = x % g.nx, row = x / g.nx;
         if (bit_at(bits_f, g.W, row, i)) parent[x] = x;
     }
 }
 
-__global__ void k_ccl_merge26(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
+__global__ void k_ccl_merge26(const uint32_t* __restrict__ bits, int* parent, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
         int i, j, k;
         decode(x, g, i, j, k);
@@ -248,7 +258,9 @@ __global__ void k_ccl_merge26(const uint32_t* __restrict__ bits_f, int* parent, 
     }
 }
 
-__global__ void k_ccl_flatten(const uint32_t* __restrict__ bits_f, int* parent, Dims g) {
+__global__ void k_ccl_flatten(const uint32_t* __restrict__ bits, int* parent, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
     const long long words = (long long)g.rows * g.W;
     for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
          gw += (long long)gridDim.x * blockDim.x) {
@@ -265,9 +277,13 @@ __global__ void k_ccl_flatten(const uint32_t* __restrict__ bits_f, int* parent, 
 }
 
 // Per block of 1024 cells: rank of each root among the block's roots.
-__global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__ bits_f,
+__global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__ bits,
                                                     const int* __restrict__ parent, int* __restrict__ rank,
-                                                    int* __restrict__ block_tot, Dims g) {
+                                                    int* __restrict__ block_tot, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
+    rank += (size_t)blockIdx.y * g.N;
+    block_tot += (size_t)blockIdx.y * (label_blocks(g) + 1);
     __shared__ int warp_tot[32];
     int x = blockIdx.x * 1024 + threadIdx.x;
     bool root = false;
@@ -296,9 +312,14 @@ __global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__
 // The same for rows of whole 32-cell words (bit word gw holds cells
 // 32 gw .. 32 gw + 31): one warp per 1024-cell block, a lane per word, and
 // only the occupied cells read their parent.
-__global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restrict__ bits_f,
+__global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restrict__ bits,
                                                          const int* __restrict__ parent, int* __restrict__ rank,
-                                                         int* __restrict__ block_tot, int nblk, long long words) {
+                                                         int* __restrict__ block_tot, int nblk, Dims g, const __grid_constant__ LabelSlots ls) {
+    const long long words = (long long)g.rows * g.W;
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
+    rank += (size_t)blockIdx.y * g.N;
+    block_tot += (size_t)blockIdx.y * (nblk + 1);
     const int lane = threadIdx.x & 31;
     const int rb = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (rb >= nblk) return;  // whole warps leave together
@@ -326,9 +347,9 @@ __global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restr
     }
 }
 
-// Exclusive scan of n block totals in one block; off[n] = total.
-__global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ tot, int* __restrict__ off,
-                                                      int n, int* total_out) {
+// Exclusive scan of n block totals by one block of 1024 threads; off[n] =
+// total.
+__device__ void scan_block(const int* __restrict__ tot, int* __restrict__ off, int n, int* total_out) {
     __shared__ int wsum[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -364,6 +385,19 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ to
         off[n] = carry;
         if (total_out) *total_out = carry;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ tot, int* __restrict__ off, int n,
+                                                      int* total_out) {
+    scan_block(tot, off, n, total_out);
+}
+
+// One block per slot (blockIdx.y): the slot's block totals into its offsets,
+// the total (the field's tag count) into n_out[field].
+__global__ void __launch_bounds__(1024) k_scan_label(const int* __restrict__ tot, int* __restrict__ off, int nb,
+                                                     int* n_out, const __grid_constant__ LabelSlots ls) {
+    const size_t o = (size_t)blockIdx.y * (nb + 1);
+    scan_block(tot + o, off + o, nb, n_out ? n_out + ls.f[blockIdx.y] : nullptr);
 }
 
 cudaError_t scan_counts(const int* counts, int* off, int n, cudaStream_t st) {
@@ -425,11 +459,17 @@ cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, 
 // Labels for rows of whole 32-cell words: a thread per word writes its 32
 // labels as eight 16-byte stores; occupied cells take 1 + the global rank
 // of their root.
-__global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __restrict__ bits_f,
+__global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __restrict__ bits,
                                                            const int* __restrict__ parent,
                                                            const int* __restrict__ rank, const int* __restrict__ off,
                                                            int* __restrict__ label, int* __restrict__ root_of,
-                                                           int root_cap, long long words) {
+                                                           int root_cap, Dims g, const __grid_constant__ LabelSlots ls) {
+    const long long words = (long long)g.rows * g.W;
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
+    rank += (size_t)blockIdx.y * g.N;
+    off += (size_t)blockIdx.y * (label_blocks(g) + 1);
+    label += (size_t)ls.f[blockIdx.y] * g.N;
     for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
          gw += (long long)gridDim.x * blockDim.x) {
         const uint32_t w = bits_f[gw];
@@ -457,9 +497,14 @@ __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __res
 
 // Labels of one row segment per warp: 0 for empty cells, 1 + rank of the
 // root for occupied ones.
-__global__ void k_ccl_relabel(const uint32_t* __restrict__ bits_f, const int* __restrict__ parent,
+__global__ void k_ccl_relabel(const uint32_t* __restrict__ bits, const int* __restrict__ parent,
                               const int* __restrict__ rank, const int* __restrict__ off, int* __restrict__ label,
-                              int* __restrict__ root_of, int root_cap, Dims g) {
+                              int* __restrict__ root_of, int root_cap, Dims g, const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
+    rank += (size_t)blockIdx.y * g.N;
+    off += (size_t)blockIdx.y * (label_blocks(g) + 1);
+    label += (size_t)ls.f[blockIdx.y] * g.N;
     const int lane = threadIdx.x & 31;
     const long long words = (long long)g.rows * g.W;
     for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < words;
@@ -478,35 +523,56 @@ __global__ void k_ccl_relabel(const uint32_t* __restrict__ bits_f, const int* __
     }
 }
 
+// The chain of six launches that tags every slot's field; root_of (the
+// root cell of tag l at root_of[l - 1], l <= root_cap) only with one slot.
+static cudaError_t label_run(const uint32_t* bits, const Dims& g, int conn, const LabelSlots& ls, int* parent,
+                             int* rank, int* block_tot, int* block_off, int* labels, int* root_of, int root_cap,
+                             int* n_out, cudaStream_t st, long long* launches) {
+    if (ls.n <= 0) return cudaSuccess;
+    if (ls.n > kLabelSlots || (root_of && ls.n != 1)) return cudaErrorInvalidValue;
+    const int nb = label_blocks(g);
+    const long long words = (long long)g.rows * g.W;
+    // the slots share the blocks a single field would get
+    const int cap = std::max(1, sm_count() * 32 / ls.n);
+    const dim3 bw(grid_for(words, 256, cap), ls.n), bc(grid_for(g.N, 256, cap), ls.n);
+    if (conn == 6) {
+        k_ccl_init_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+        k_ccl_merge_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+    } else {
+        k_ccl_init<<<bc, 256, 0, st>>>(bits, parent, g, ls);
+        k_ccl_merge26<<<bc, 256, 0, st>>>(bits, parent, g, ls);
+    }
+    k_ccl_flatten<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+    // rows of whole words (and a 16-byte-aligned label array): word-wise passes
+    const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)labels & 15) == 0;
+    if (wordwise)
+        k_ccl_count_words<<<dim3((nb + 7) / 8, ls.n), 256, 0, st>>>(bits, parent, rank, block_tot, nb, g, ls);
+    else
+        k_ccl_count<<<dim3(nb, ls.n), 1024, 0, st>>>(bits, parent, rank, block_tot, g, ls);
+    k_scan_label<<<dim3(1, ls.n), 1024, 0, st>>>(block_tot, block_off, nb, n_out, ls);
+    if (wordwise)
+        k_ccl_relabel_words<<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g, ls);
+    else
+        k_ccl_relabel<<<dim3(grid_for(words * 32, 256, cap), ls.n), 256, 0, st>>>(bits, parent, rank, block_off,
+                                                                                 labels, root_of, root_cap, g, ls);
+    if (launches) *launches += 6;
+    return cudaGetLastError();
+}
+
 cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
                         int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
                         cudaStream_t st, long long* launches) {
-    int nb = (g.N + 1023) / 1024;
-    long long words = (long long)g.rows * g.W;
-    int bw = grid_for(words, 256);
-    if (conn == 6) {
-        k_ccl_init_runs<<<bw, 256, 0, st>>>(bits_f, parent, g);
-        k_ccl_merge_runs<<<bw, 256, 0, st>>>(bits_f, parent, g);
-    } else {
-        k_ccl_init<<<grid_for(g.N, 256), 256, 0, st>>>(bits_f, parent, g);
-        k_ccl_merge26<<<grid_for(g.N, 256), 256, 0, st>>>(bits_f, parent, g);
-    }
-    k_ccl_flatten<<<bw, 256, 0, st>>>(bits_f, parent, g);
-    // rows of whole words (and a 16-byte-aligned label array): word-wise passes
-    const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)label & 15) == 0;
-    if (wordwise)
-        k_ccl_count_words<<<(nb + 7) / 8, 256, 0, st>>>(bits_f, parent, rank, block_tot, nb, words);
-    else
-        k_ccl_count<<<nb, 1024, 0, st>>>(bits_f, parent, rank, block_tot, g);
-    k_scan_blocks<<<1, 1024, 0, st>>>(block_tot, block_off, nb, n_out);
-    if (wordwise)
-        k_ccl_relabel_words<<<grid_for(words, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
-                                                                  root_cap, words);
-    else
-        k_ccl_relabel<<<grid_for(words * 32, 256), 256, 0, st>>>(bits_f, parent, rank, block_off, label, root_of,
-                                                                 root_cap, g);
-    if (launches) *launches += 6;
-    return cudaGetLastError();
+    LabelSlots one{};
+    one.n = 1;
+    one.f[0] = 0;
+    return label_run(bits_f, g, conn, one, parent, rank, block_tot, block_off, label, root_of, root_cap, n_out, st,
+                     launches);
+}
+
+cudaError_t label_fields(const uint32_t* bits, const Dims& g, int conn, const LabelSlots& ls, int* parent, int* rank,
+                         int* block_tot, int* block_off, int* labels, int* n_out, cudaStream_t st,
+                         long long* launches) {
+    return label_run(bits, g, conn, ls, parent, rank, block_tot, block_off, labels, nullptr, 0, n_out, st, launches);
 }
 
 // --------------------------------------------------------------------------
@@ -530,10 +596,14 @@ __device__ __forceinline__ void set_insert(unsigned long long* table, int mask, 
     atomicExch(overflow, 1);
 }
 
-__global__ void k_pairs(const uint32_t* __restrict__ ncmap_f, const uint32_t* __restrict__ bits_f,
-                        const int* __restrict__ label_f, Dims g, int w, int f,
-                        unsigned long long* table, int mask, int* overflow) {
-    long long words = (long long)g.rows * g.W;
+__global__ void k_pairs(const uint32_t* __restrict__ ncmap, const uint32_t* __restrict__ bits,
+                        const int* __restrict__ labels, Dims g, int w, unsigned long long* table, int mask,
+                        int* overflow, const __grid_constant__ LabelSlots ls) {
+    const long long words = (long long)g.rows * g.W;
+    const int f = ls.f[blockIdx.y];
+    const uint32_t* ncmap_f = ncmap + (size_t)f * words;
+    const uint32_t* bits_f = bits + (size_t)f * words;
+    const int* label_f = labels + (size_t)f * g.N;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words;
          idx += (long long)gridDim.x * blockDim.x) {
         uint32_t m = ncmap_f[idx];
@@ -569,10 +639,14 @@ __global__ void k_compact_set(const unsigned long long* __restrict__ table, int 
     }
 }
 
-cudaError_t tag_pairs(const uint32_t* ncmap_f, const uint32_t* bits_f, const int* label_f, const Dims& g,
-                      int w, int f, unsigned long long* table, int cap, int* overflow, cudaStream_t st) {
-    long long words = (long long)g.rows * g.W;
-    k_pairs<<<grid_for(words, 128), 128, 0, st>>>(ncmap_f, bits_f, label_f, g, w, f, table, cap - 1, overflow);
+cudaError_t tag_pairs_fields(const uint32_t* ncmap, const uint32_t* bits, const int* labels, const Dims& g, int w,
+                             const LabelSlots& ls, unsigned long long* table, int cap, int* overflow,
+                             cudaStream_t st) {
+    if (ls.n <= 0) return cudaSuccess;
+    if (ls.n > kLabelSlots) return cudaErrorInvalidValue;
+    const long long words = (long long)g.rows * g.W;
+    const int blocks = grid_for(words, 128, std::max(1, sm_count() * 32 / ls.n));
+    k_pairs<<<dim3(blocks, ls.n), 128, 0, st>>>(ncmap, bits, labels, g, w, table, cap - 1, overflow, ls);
     return cudaGetLastError();
 }
 
