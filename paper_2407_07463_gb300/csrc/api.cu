@@ -447,7 +447,7 @@ vof_status stats_accumulate(vof_ctx* ctx, long long* D_out, double* vtot_out) {
         if (D + n > kDropCap) return VOF_ERR_CAPACITY;
         if (n > 0) {
             VOF_CUDA(ctx, cudaMemsetAsync(S + 4 * D, 0, (size_t)n * 4 * 8, st));
-            VOF_CUDA(ctx, drop_sums(cfp, ctx->fp64, lab, ctx->slot<int>(S_PARENT), g, S + 4 * D, n, st));
+            VOF_CUDA(ctx, drop_sums(cfp, ctx->fp64, lab, root + D, g, S + 4 * D, n, st));
             VOF_CUDA(ctx, drop_finalize(S + 4 * D, root + D, g, cf.h, n, vol + D, cen + 3 * D, st));
             VOF_CUDA(ctx, drop_inertia(cfp, ctx->fp64, lab, g, cf.h, cen + 3 * D, n, shape + 6 * D, st));
             ctx->launches += 4;
@@ -764,7 +764,7 @@ vof_status vof_drop_table(vof_ctx* ctx, int32_t field, const int32_t* label_dev,
                               ctx->slot<int>(S_ROOT), kDropCap, nout + field, ctx->stream, &ctx->launches));
     double* S = ctx->slot<double>(S_DSUM);
     VOF_CUDA(ctx, cudaMemsetAsync(S, 0, (size_t)n_labels * 4 * 8, ctx->stream));
-    VOF_CUDA(ctx, drop_sums(cf, ctx->fp64, label_dev, ctx->slot<int>(S_PARENT), g, S, n_labels, ctx->stream));
+    VOF_CUDA(ctx, drop_sums(cf, ctx->fp64, label_dev, ctx->slot<int>(S_ROOT), g, S, n_labels, ctx->stream));
     VOF_CUDA(ctx, drop_finalize(S, ctx->slot<int>(S_ROOT), g, ctx->cfg.h, n_labels, vol_dev, cen_dev, ctx->stream));
     ctx->launches += 3;
     return VOF_OK;

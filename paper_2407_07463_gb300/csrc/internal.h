@@ -117,6 +117,11 @@ cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, i
 // occupied cell (flags cleared by the caller).
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
                          cudaStream_t st);
+// Tags of one field's occupancy bits: label (0 empty, else 1 + the rank of
+// the component's root, its smallest cell), *n_out the tag count, root_of[l
+// - 1] the root cell of tag l <= root_cap (if not null).  parent, rank,
+// block_tot and block_off are scratch: parent does not hold every cell's
+// root afterwards.
 cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* parent, int* rank,
                         int* block_tot, int* block_off, int* label, int* root_of, int root_cap, int* n_out,
                         cudaStream_t st, long long* launches);
@@ -160,7 +165,9 @@ cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t*
                           MoveTables mt, const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);
 
 // Statistics helpers.
-cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* parent, const Dims& g,
+// Per tag l <= n_max: the sum of c and its first moments about the tag's
+// root cell root_of[l - 1] (minimum image), into S[4 (l - 1) ..].
+cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* root_of, const Dims& g,
                       double* S, int n_max, cudaStream_t st);
 cudaError_t drop_finalize(const double* S, const int* root_of, const Dims& g, double h, int n,
                           double* vol, double* cen, cudaStream_t st);

@@ -284,11 +284,11 @@ cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t*
 
 template <typename T>
 __global__ void k_drop_sums(const T* __restrict__ cf, const int* __restrict__ label_f,
-                            const int* __restrict__ parent, Dims g, double* __restrict__ S, int n_max) {
+                            const int* __restrict__ root_of, Dims g, double* __restrict__ S, int n_max) {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.N; x += gridDim.x * blockDim.x) {
         int l = label_f[x];
         if (l <= 0 || l > n_max) continue;
-        int r = parent[x];
+        int r = root_of[l - 1];
         int i, j, k, ri, rj, rk;
         decode(x, g, i, j, k);
         decode(r, g, ri, rj, rk);
@@ -308,12 +308,12 @@ __global__ void k_drop_sums(const T* __restrict__ cf, const int* __restrict__ la
     }
 }
 
-cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* parent, const Dims& g,
+cudaError_t drop_sums(const void* cf, bool fp64, const int* label_f, const int* root_of, const Dims& g,
                       double* S, int n_max, cudaStream_t st) {
     if (fp64)
-        k_drop_sums<double><<<grid_for(g.N, 256), 256, 0, st>>>((const double*)cf, label_f, parent, g, S, n_max);
+        k_drop_sums<double><<<grid_for(g.N, 256), 256, 0, st>>>((const double*)cf, label_f, root_of, g, S, n_max);
     else
-        k_drop_sums<float><<<grid_for(g.N, 256), 256, 0, st>>>((const float*)cf, label_f, parent, g, S, n_max);
+        k_drop_sums<float><<<grid_for(g.N, 256), 256, 0, st>>>((const float*)cf, label_f, root_of, g, S, n_max);
     return cudaGetLastError();
 }
 

@@ -276,6 +276,39 @@ __global__ void k_ccl_flatten(const uint32_t* __restrict__ bits, int* parent, Di
     }
 }
 
+// Heads of the runs of a row word w: the run starts, plus bit 0 where a run
+// continues from the row's previous word (carry: that word's last bit).
+__device__ __forceinline__ uint32_t run_starts(uint32_t w, uint32_t carry) { return w & ~((w << 1) | carry); }
+__device__ __forceinline__ uint32_t run_heads(uint32_t w, uint32_t carry) { return run_starts(w, carry) | (w & carry); }
+// The head of the run holding bit b of a word with heads h.
+__device__ __forceinline__ int head_of(uint32_t h, int b) {
+    return 31 - __clz(h & (b == 31 ? 0xffffffffu : ((2u << b) - 1u)));
+}
+
+// Flattening for the run-based links of 6-connectivity: only the head of
+// every run of every word takes its root (a run's other cells link to their
+// head, or to the previous word, and are labelled through their head).
+__global__ void k_ccl_flatten_runs(const uint32_t* __restrict__ bits, int* parent, Dims g,
+                                   const __grid_constant__ LabelSlots ls) {
+    const uint32_t* bits_f = slot_bits(bits, ls, g);
+    parent += (size_t)blockIdx.y * g.N;
+    const long long words = (long long)g.rows * g.W;
+    for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
+         gw += (long long)gridDim.x * blockDim.x) {
+        const uint32_t w = bits_f[gw];
+        if (!w) continue;
+        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const uint32_t carry = wi > 0 ? (bits_f[gw - 1] >> 31) : 0u;
+        uint32_t h = run_heads(w, carry);
+        const int x0 = row * g.nx + wi * 32;
+        while (h) {
+            const int b = __ffs(h) - 1;
+            h &= h - 1u;
+            parent[x0 + b] = find_root(parent, x0 + b);
+        }
+    }
+}
+
 // Per block of 1024 cells: rank of each root among the block's roots.
 __global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__ bits,
                                                     const int* __restrict__ parent, int* __restrict__ rank,
@@ -312,6 +345,9 @@ __global__ void __launch_bounds__(1024) k_ccl_count(const uint32_t* __restrict__
 // The same for rows of whole 32-cell words (bit word gw holds cells
 // 32 gw .. 32 gw + 31): one warp per 1024-cell block, a lane per word, and
 // only the occupied cells read their parent.
+// RUNS: the run-based links of 6-connectivity, where only run starts can be
+// roots.
+template <bool RUNS>
 __global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restrict__ bits,
                                                          const int* __restrict__ parent, int* __restrict__ rank,
                                                          int* __restrict__ block_tot, int nblk, Dims g, const __grid_constant__ LabelSlots ls) {
@@ -326,6 +362,7 @@ __global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restr
     const long long gw = (long long)rb * 32 + lane;
     uint32_t m = gw < words ? bits_f[gw] : 0u, rm = 0u;
     const int x0 = (int)(gw * 32);
+    if (RUNS && m) m = run_starts(m, (gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1u;
@@ -459,6 +496,8 @@ cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, 
 // Labels for rows of whole 32-cell words: a thread per word writes its 32
 // labels as eight 16-byte stores; occupied cells take 1 + the global rank
 // of their root.
+// RUNS: run-based links, where a cell's root is that of its run's head.
+template <bool RUNS>
 __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __restrict__ bits,
                                                            const int* __restrict__ parent,
                                                            const int* __restrict__ rank, const int* __restrict__ off,
@@ -475,6 +514,9 @@ __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __res
         const uint32_t w = bits_f[gw];
         const int x0 = (int)(gw * 32);
         int4* dst = reinterpret_cast<int4*>(label + x0);
+        uint32_t heads = 0u;
+        if (RUNS && w) heads = run_heads(w, (gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
+        int last_head = -1, last_l = 0;  // the cells of a run share their head's tag
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             int l4[4];
@@ -484,9 +526,20 @@ __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __res
                 int l = 0;
                 if ((w >> b) & 1u) {
                     const int x = x0 + b;
-                    const int r = parent[x];
-                    l = off[r >> 10] + rank[r] + 1;
-                    if (r == x && root_of && l <= root_cap) root_of[l - 1] = x;
+                    if (RUNS) {
+                        const int h = head_of(heads, b);
+                        if (h != last_head) {
+                            const int r = parent[x0 + h];
+                            last_l = off[r >> 10] + rank[r] + 1;
+                            last_head = h;
+                            if (r == x && root_of && last_l <= root_cap) root_of[last_l - 1] = x;
+                        }
+                        l = last_l;
+                    } else {
+                        const int r = parent[x];
+                        l = off[r >> 10] + rank[r] + 1;
+                        if (r == x && root_of && l <= root_cap) root_of[l - 1] = x;
+                    }
                 }
                 l4[e] = l;
             }
@@ -542,16 +595,27 @@ static cudaError_t label_run(const uint32_t* bits, const Dims& g, int conn, cons
         k_ccl_init<<<bc, 256, 0, st>>>(bits, parent, g, ls);
         k_ccl_merge26<<<bc, 256, 0, st>>>(bits, parent, g, ls);
     }
-    k_ccl_flatten<<<bw, 256, 0, st>>>(bits, parent, g, ls);
-    // rows of whole words (and a 16-byte-aligned label array): word-wise passes
+    // rows of whole words (and a 16-byte-aligned label array): word-wise
+    // passes; with run-based links only the heads of runs are flattened
     const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)labels & 15) == 0;
-    if (wordwise)
-        k_ccl_count_words<<<dim3((nb + 7) / 8, ls.n), 256, 0, st>>>(bits, parent, rank, block_tot, nb, g, ls);
+    const bool runs = wordwise && conn == 6;
+    if (runs)
+        k_ccl_flatten_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+    else
+        k_ccl_flatten<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+    const dim3 bcnt((nb + 7) / 8, ls.n);
+    if (runs)
+        k_ccl_count_words<true><<<bcnt, 256, 0, st>>>(bits, parent, rank, block_tot, nb, g, ls);
+    else if (wordwise)
+        k_ccl_count_words<false><<<bcnt, 256, 0, st>>>(bits, parent, rank, block_tot, nb, g, ls);
     else
         k_ccl_count<<<dim3(nb, ls.n), 1024, 0, st>>>(bits, parent, rank, block_tot, g, ls);
     k_scan_label<<<dim3(1, ls.n), 1024, 0, st>>>(block_tot, block_off, nb, n_out, ls);
-    if (wordwise)
-        k_ccl_relabel_words<<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g, ls);
+    if (runs)
+        k_ccl_relabel_words<true><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g, ls);
+    else if (wordwise)
+        k_ccl_relabel_words<false><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g,
+                                                        ls);
     else
         k_ccl_relabel<<<dim3(grid_for(words * 32, 256, cap), ls.n), 256, 0, st>>>(bits, parent, rank, block_off,
                                                                                  labels, root_of, root_cap, g, ls);
