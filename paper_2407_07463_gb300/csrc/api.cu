@@ -255,12 +255,16 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
     if (fired_out) *fired_out = 0;
 
     // Step 1 on the snapshot
-    if (!ctx->bits_valid)
+    if (!ctx->bits_valid) {
         VOF_CUDA(ctx, timed(ctx, P_PACK_BITS, [&] { return pack_bits(ctx->cur, ctx->fp64, bits, g, na0, occupancy_tau(ctx), st); }));
+        ctx->launches += 1;
+    }
     if (na0 < K) VOF_CUDA(ctx, cudaMemsetAsync(bits + (size_t)na0 * words, 0, (size_t)(K - na0) * words * 4, st));
     VOF_CUDA(ctx, cudaMemsetAsync(flags, 0, kMaxK * sizeof(int), st));
-    VOF_CUDA(ctx, timed(ctx, P_NEAR_CONTACT, [&] { return near_contact(bits, ncmap, flags, g, na0, cf.stencil_w, st); }));
-    ctx->launches += 2;
+    VOF_CUDA(ctx, timed(ctx, P_NEAR_CONTACT, [&] {
+                 return near_contact(bits, ncmap, flags, g, na0, cf.stencil_w, st);
+             }));
+    ctx->launches += 1;
     int hflags[kMaxK];
     VOF_CUDA(ctx, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     VOF_CUDA(ctx, cudaStreamSynchronize(st));

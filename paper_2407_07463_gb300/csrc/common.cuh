@@ -37,6 +37,9 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
+// i mod n for -n <= i < 2n (an index at most one period outside [0, n)).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 __device__ __forceinline__ void decode(int x, const Dims& g, int& i, int& j, int& k) {
     i = x % g.nx;
     int r = x / g.nx;

@@ -113,6 +113,10 @@ constexpr int kFaceTile = 128;
 cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, int tile_cap, cudaStream_t st);
 cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, int K, double tau,
                       cudaStream_t st);
+// Box dilation (Chebyshev distance reach, periodic) of n bit planes from src
+// into dst; tmp: n planes of scratch.
+cudaError_t dilate_planes(const uint32_t* src, uint32_t* dst, uint32_t* tmp, int n, const Dims& g, int reach,
+                          cudaStream_t st);
 // Step 1 per field: flags[f] |= 1 if it fired, |= 2 if the field holds an
 // occupied cell (flags cleared by the caller).
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
@@ -129,7 +133,8 @@ cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* pa
 // f[s]).  A field's bit plane, near-contact map and labels sit f * words and
 // f * N from their bases and its drop count at n_out[f]; a slot's scratch
 // sits s * N (parent, rank) and s * (nb + 1) (block totals and offsets, nb =
-// ceil(N / 1024)) from theirs.
+// ceil(N / 1024)) from theirs.  Labels are complete only at occupied cells
+// (empty cells of a row word without an occupied cell keep what they held).
 constexpr int kLabelSlots = 16;
 struct LabelSlots {
     int n;

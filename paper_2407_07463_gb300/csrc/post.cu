@@ -38,11 +38,11 @@ __global__ void __launch_bounds__(256) k_moving_bits(const int* __restrict__ lab
     for (long long wd = (long long)blockIdx.x * blockDim.x + threadIdx.x; wd < words;
          wd += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(wd / per_field);
-        const long long rem = wd - (long long)q * per_field;
+        const int rem = (int)(wd - (long long)q * per_field);
         const int f = mv_fields[q];
         uint32_t occ = bits[(size_t)f * per_field + rem], mv = 0u;
         if (occ) {
-            const int row = (int)(rem / g.W), wi = (int)(rem - (long long)row * g.W);
+            const int row = rem / g.W, wi = rem - row * g.W;
             const int* lab = labels + (size_t)f * g.N + (size_t)row * g.nx + wi * 32;
             while (occ) {
                 const int b = __ffs(occ) - 1;
@@ -59,65 +59,6 @@ __global__ void __launch_bounds__(256) k_moving_bits(const int* __restrict__ lab
 __device__ __forceinline__ unsigned long long row_window64(const uint32_t* __restrict__ row, int W, int nx, int x0) {
     return (unsigned long long)row_window(row, W, nx, x0) |
            ((unsigned long long)row_window(row, W, nx, x0 + 32) << 32);
-}
-
-// Box dilation of bit planes (plane blockIdx.y at blockIdx.y * per-field
-// words), one axis per pass, periodic: a cell of dst is set when a cell of
-// src within `reach` of it along the pass's axis is.  The three passes give
-// the cells within Chebyshev distance `reach` of a set cell.
-__global__ void __launch_bounds__(256) k_dilate_x(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                                                  Dims g, int reach) {
-    const long long pf = (long long)g.rows * g.W;
-    src += (size_t)blockIdx.y * pf;
-    dst += (size_t)blockIdx.y * pf;
-    const bool aligned = (g.nx & 31) == 0;
-    const uint32_t tail = (g.nx & 31) ? (1u << (g.nx & 31)) - 1u : 0xffffffffu;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
-         w += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(w / g.W), wi = (int)(w - (long long)row * g.W);
-        const uint32_t* r = src + (size_t)row * g.W;
-        uint32_t acc = 0u;
-        if (aligned) {
-            const uint32_t l = r[wi == 0 ? g.W - 1 : wi - 1], c = r[wi], h = r[wi + 1 == g.W ? 0 : wi + 1];
-            if (l | c | h)
-                for (int dx = -reach; dx <= reach; ++dx) acc |= shift_window(l, c, h, dx);
-        } else {
-            for (int dx = -reach; dx <= reach; ++dx) acc |= row_window(r, g.W, g.nx, wi * 32 + dx);
-            if (wi == g.W - 1) acc &= tail;
-        }
-        dst[w] = acc;
-    }
-}
-
-// axis 1: along y, axis 2: along z
-__global__ void __launch_bounds__(256) k_dilate_rows(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
-                                                     Dims g, int reach, int axis) {
-    const long long pf = (long long)g.rows * g.W;
-    src += (size_t)blockIdx.y * pf;
-    dst += (size_t)blockIdx.y * pf;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
-         w += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(w / g.W), wi = (int)(w - (long long)row * g.W);
-        const int j = row % g.ny, k = row / g.ny;
-        uint32_t acc = 0u;
-        for (int dd = -reach; dd <= reach; ++dd) {
-            const int rr = axis == 1 ? k * g.ny + wrapi(j + dd, g.ny) : wrapi(k + dd, g.nz) * g.ny + j;
-            acc |= src[(size_t)rr * g.W + wi];
-        }
-        dst[w] = acc;
-    }
-}
-
-// Dilation of n planes from src into dst (tmp: n planes of scratch).
-static cudaError_t dilate_planes(const uint32_t* src, uint32_t* dst, uint32_t* tmp, int n, const Dims& g, int reach,
-                                 cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const long long pf = (long long)g.rows * g.W;
-    const dim3 grid(grid_for(pf, 256, std::max(1, sm_count() * 32 / n)), n);
-    k_dilate_x<<<grid, 256, 0, st>>>(src, dst, g, reach);
-    k_dilate_rows<<<grid, 256, 0, st>>>(dst, tmp, g, reach, 1);
-    k_dilate_rows<<<grid, 256, 0, st>>>(tmp, dst, g, reach, 2);
-    return cudaGetLastError();
 }
 
 // For every moving drop m: the fields (other than its own) with an occupied

@@ -50,6 +50,67 @@ cudaError_t pack_bits(const void* c, bool fp64, uint32_t* bits, const Dims& g, i
 }
 
 // --------------------------------------------------------------------------
+// Box dilation of bit planes (plane blockIdx.y at blockIdx.y * per-field
+// words), one axis per pass, periodic: a cell of dst is set when a cell of
+// src within `reach` of it along the pass's axis is.  The three passes give
+// the cells within Chebyshev distance `reach` of a set cell.
+__global__ void __launch_bounds__(256) k_dilate_x(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                  Dims g, int reach) {
+    const long long pf = (long long)g.rows * g.W;
+    src += (size_t)blockIdx.y * pf;
+    dst += (size_t)blockIdx.y * pf;
+    const bool aligned = (g.nx & 31) == 0;
+    const uint32_t tail = (g.nx & 31) ? (1u << (g.nx & 31)) - 1u : 0xffffffffu;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)w / g.W, wi = (int)w - row * g.W;
+        const uint32_t* r = src + (size_t)row * g.W;
+        uint32_t acc = 0u;
+        if (aligned) {
+            const uint32_t l = r[wi == 0 ? g.W - 1 : wi - 1], c = r[wi], h = r[wi + 1 == g.W ? 0 : wi + 1];
+            if (l | c | h)
+                for (int dx = -reach; dx <= reach; ++dx) acc |= shift_window(l, c, h, dx);
+        } else {
+            for (int dx = -reach; dx <= reach; ++dx) acc |= row_window(r, g.W, g.nx, wi * 32 + dx);
+            if (wi == g.W - 1) acc &= tail;
+        }
+        dst[w] = acc;
+    }
+}
+
+// axis 1: along y, axis 2: along z
+__global__ void __launch_bounds__(256) k_dilate_rows(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                     Dims g, int reach, int axis) {
+    const long long pf = (long long)g.rows * g.W;
+    src += (size_t)blockIdx.y * pf;
+    dst += (size_t)blockIdx.y * pf;
+    const bool near = reach < (axis == 1 ? g.ny : g.nz);
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < pf;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)w / g.W, wi = (int)w - row * g.W;
+        const int k = row / g.ny, j = row - k * g.ny;
+        uint32_t acc = 0u;
+        for (int dd = -reach; dd <= reach; ++dd) {
+            const int rr = axis == 1 ? k * g.ny + (near ? wrap1(j + dd, g.ny) : wrapi(j + dd, g.ny))
+                                     : (near ? wrap1(k + dd, g.nz) : wrapi(k + dd, g.nz)) * g.ny + j;
+            acc |= src[(size_t)rr * g.W + wi];
+        }
+        dst[w] = acc;
+    }
+}
+
+cudaError_t dilate_planes(const uint32_t* src, uint32_t* dst, uint32_t* tmp, int n, const Dims& g, int reach,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long pf = (long long)g.rows * g.W;
+    const dim3 grid(grid_for(pf, 256, std::max(1, sm_count() * 32 / n)), n);
+    k_dilate_x<<<grid, 256, 0, st>>>(src, dst, g, reach);
+    k_dilate_rows<<<grid, 256, 0, st>>>(dst, tmp, g, reach, 1);
+    k_dilate_rows<<<grid, 256, 0, st>>>(tmp, dst, g, reach, 2);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
 // Step 1: near contact.  For every cell with c <= tau, is there an offset
 // delta in [-w,w]^3 \ {0} with both cells x + delta and x - delta occupied?
 // One offset per opposite pair: the first nonzero of (dz, dy, dx) positive.
@@ -119,11 +180,83 @@ __global__ void __launch_bounds__(256) k_near_contact(const uint32_t* __restrict
     }
 }
 
+// The same test on tiles of whole rows, for rows of a power-of-two number
+// W <= 32 of whole words: a block of 256 threads takes 256 / W rows of one
+// field (TY = 2^ty_log along y by TZ along z, one word per thread), stages
+// them with a halo of w rows along y and z in shared memory, and reads every
+// neighbour row from there.
+constexpr int kNcThreads = 256;
+__global__ void __launch_bounds__(kNcThreads) k_near_contact_tile(const uint32_t* __restrict__ bits,
+                                                                  uint32_t* __restrict__ ncmap,
+                                                                  int* __restrict__ flags, Dims g, int w, int lw,
+                                                                  int ty_log, int tiles_y) {
+    extern __shared__ uint32_t s_rows[];
+    const int f = blockIdx.y;
+    const int W = 1 << lw;
+    const int TY = 1 << ty_log, TZ = (kNcThreads >> lw) >> ty_log;
+    const int HY = TY + 2 * w, HZ = TZ + 2 * w;
+    const int tz = blockIdx.x / tiles_y, tyi = blockIdx.x - tz * tiles_y;
+    const int j0 = tyi * TY, k0 = tz * TZ;
+    const size_t per_field = (size_t)g.rows * W;
+    const uint32_t* fb = bits + (size_t)f * per_field;
+    // the tile's rows and their halo (the caller ensures TY + w <= ny and
+    // TZ + w <= nz, so every staged index is within one period)
+    for (int t = threadIdx.x; t < HY * HZ * W; t += kNcThreads) {
+        const int wi = t & (W - 1), r = t >> lw;
+        const int hz = r / HY, hy = r - hz * HY;
+        const int j = wrap1(j0 - w + hy, g.ny), k = wrap1(k0 - w + hz, g.nz);
+        s_rows[t] = fb[(size_t)(k * g.ny + j) * W + wi];
+    }
+    __syncthreads();
+    const int wi = threadIdx.x & (W - 1), r = threadIdx.x >> lw;
+    const int lz = r >> ty_log, ly = r - (lz << ty_log);
+    const int j = j0 + ly, k = k0 + lz;
+    if (j >= g.ny || k >= g.nz) return;  // a partial tile at the grid's end
+    const uint32_t* base = s_rows + ((size_t)(lz + w) * HY + (ly + w)) * W;
+    const uint32_t centre = base[wi];
+    const uint32_t empty = ~centre;
+    const int wl = (wi - 1) & (W - 1), wr = (wi + 1) & (W - 1);
+    uint32_t acc = 0;
+    if (empty) {
+        for (int dz = 0; dz <= w && (acc & empty) != empty; ++dz) {
+            for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy) {
+                const uint32_t* ra = base + (dz * HY + dy) * W;
+                const uint32_t* rb = base - (dz * HY + dy) * W;
+                const uint32_t al = ra[wl], ac = ra[wi], ar = ra[wr];
+                const uint32_t bl = rb[wl], bc = rb[wi], br = rb[wr];
+                if (((al | ac | ar) == 0) || ((bl | bc | br) == 0)) continue;
+                for (int dx = (dz == 0 && dy == 0) ? 1 : -w; dx <= w; ++dx)
+                    acc |= shift_window(al, ac, ar, dx) & shift_window(bl, bc, br, -dx);
+            }
+        }
+    }
+    const uint32_t res = acc & empty;
+    if (ncmap) ncmap[(size_t)f * per_field + (size_t)(k * g.ny + j) * W + wi] = res;
+    if (res && (*(volatile int*)&flags[f] & 1) == 0) atomicOr(&flags[f], 1);
+    if (centre && (*(volatile int*)&flags[f] & 2) == 0) atomicOr(&flags[f], 2);
+}
+
 cudaError_t near_contact(const uint32_t* bits, uint32_t* ncmap, int* flags, const Dims& g, int K, int w,
                          cudaStream_t st) {
     if (K <= 0) return cudaSuccess;
     const long long per_field = (long long)g.rows * g.W;
-    k_near_contact<<<dim3(grid_for(per_field, 256, sm_count() * 32 / K + 1), K), 256, 0, st>>>(bits, ncmap, flags, g, K, w);
+    int lw = 0;
+    while ((1 << lw) < g.W) ++lw;
+    const int R = kNcThreads >> lw;  // rows per tile
+    int ty_log = 0;
+    while ((1 << (2 * (ty_log + 1))) <= R) ++ty_log;  // TY ~ sqrt(R)
+    const int TY = 1 << ty_log, TZ = R / TY;
+    const bool tiled = (g.nx & 31) == 0 && (1 << lw) == g.W && g.W <= 32 && w >= 1 && w <= 4 && TY + w <= g.ny &&
+                       TZ + w <= g.nz && w < g.ny && w < g.nz;
+    if (tiled) {
+        const int tiles_y = (g.ny + TY - 1) / TY, tiles_z = (g.nz + TZ - 1) / TZ;
+        const size_t smem = (size_t)(TY + 2 * w) * (TZ + 2 * w) * g.W * sizeof(uint32_t);
+        k_near_contact_tile<<<dim3(tiles_y * tiles_z, K), kNcThreads, smem, st>>>(bits, ncmap, flags, g, w, lw, ty_log,
+                                                                                 tiles_y);
+    } else {
+        k_near_contact<<<dim3(grid_for(per_field, 256, sm_count() * 32 / K + 1), K), 256, 0, st>>>(bits, ncmap, flags,
+                                                                                                   g, K, w);
+    }
     return cudaGetLastError();
 }
 
@@ -179,7 +312,7 @@ __global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits, int* __restri
          gw += (long long)gridDim.x * blockDim.x) {
         const uint32_t w = bits_f[gw];
         if (!w) continue;
-        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const uint32_t carry = wi > 0 ? (bits_f[gw - 1] >> 31) : 0u;
         const uint32_t starts = w & ~((w << 1) | carry);
         const int x0 = row * g.nx + wi * 32;
@@ -212,7 +345,7 @@ __global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits, int* parent,
          gw += (long long)gridDim.x * blockDim.x) {
         const uint32_t w = bits_f[gw];
         if (!w) continue;
-        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const int j = row % g.ny, k = row / g.ny;
         const int x0 = row * g.nx + wi * 32;
         if (wi == 0 && (w & 1u) && g.nx > 1) {
@@ -266,7 +399,7 @@ __global__ void k_ccl_flatten(const uint32_t* __restrict__ bits, int* parent, Di
          gw += (long long)gridDim.x * blockDim.x) {
         uint32_t m = bits_f[gw];
         if (!m) continue;
-        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const int x0 = row * g.nx + wi * 32;
         while (m) {
             const int b = __ffs(m) - 1;
@@ -297,7 +430,7 @@ __global__ void k_ccl_flatten_runs(const uint32_t* __restrict__ bits, int* paren
          gw += (long long)gridDim.x * blockDim.x) {
         const uint32_t w = bits_f[gw];
         if (!w) continue;
-        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const uint32_t carry = wi > 0 ? (bits_f[gw - 1] >> 31) : 0u;
         uint32_t h = run_heads(w, carry);
         const int x0 = row * g.nx + wi * 32;
@@ -362,7 +495,7 @@ __global__ void __launch_bounds__(256) k_ccl_count_words(const uint32_t* __restr
     const long long gw = (long long)rb * 32 + lane;
     uint32_t m = gw < words ? bits_f[gw] : 0u, rm = 0u;
     const int x0 = (int)(gw * 32);
-    if (RUNS && m) m = run_starts(m, (gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
+    if (RUNS && m) m = run_starts(m, ((int)gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1u;
@@ -497,7 +630,9 @@ cudaError_t scan_face_counts(const int* counts, int* off, int n, int* tile_seg, 
 // labels as eight 16-byte stores; occupied cells take 1 + the global rank
 // of their root.
 // RUNS: run-based links, where a cell's root is that of its run's head.
-template <bool RUNS>
+// SPARSE: words without an occupied cell are not written (their labels are
+// left as they were), for callers that read labels only at occupied cells.
+template <bool RUNS, bool SPARSE>
 __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __restrict__ bits,
                                                            const int* __restrict__ parent,
                                                            const int* __restrict__ rank, const int* __restrict__ off,
@@ -512,10 +647,11 @@ __global__ void __launch_bounds__(256) k_ccl_relabel_words(const uint32_t* __res
     for (long long gw = (long long)blockIdx.x * blockDim.x + threadIdx.x; gw < words;
          gw += (long long)gridDim.x * blockDim.x) {
         const uint32_t w = bits_f[gw];
+        if (SPARSE && !w) continue;
         const int x0 = (int)(gw * 32);
         int4* dst = reinterpret_cast<int4*>(label + x0);
         uint32_t heads = 0u;
-        if (RUNS && w) heads = run_heads(w, (gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
+        if (RUNS && w) heads = run_heads(w, ((int)gw % g.W) ? (bits_f[gw - 1] >> 31) : 0u);
         int last_head = -1, last_l = 0;  // the cells of a run share their head's tag
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -562,7 +698,7 @@ __global__ void k_ccl_relabel(const uint32_t* __restrict__ bits, const int* __re
     const long long words = (long long)g.rows * g.W;
     for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < words;
          gw += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const int row = (int)(gw / g.W), wi = (int)(gw - (long long)row * g.W);
+        const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const int i = wi * 32 + lane;
         if (i >= g.nx) continue;
         const int x = row * g.nx + i;
@@ -578,9 +714,10 @@ __global__ void k_ccl_relabel(const uint32_t* __restrict__ bits, const int* __re
 
 // The chain of six launches that tags every slot's field; root_of (the
 // root cell of tag l at root_of[l - 1], l <= root_cap) only with one slot.
+// sparse: labels are needed only at occupied cells.
 static cudaError_t label_run(const uint32_t* bits, const Dims& g, int conn, const LabelSlots& ls, int* parent,
                              int* rank, int* block_tot, int* block_off, int* labels, int* root_of, int root_cap,
-                             int* n_out, cudaStream_t st, long long* launches) {
+                             int* n_out, bool sparse, cudaStream_t st, long long* launches) {
     if (ls.n <= 0) return cudaSuccess;
     if (ls.n > kLabelSlots || (root_of && ls.n != 1)) return cudaErrorInvalidValue;
     const int nb = label_blocks(g);
@@ -611,11 +748,15 @@ static cudaError_t label_run(const uint32_t* bits, const Dims& g, int conn, cons
     else
         k_ccl_count<<<dim3(nb, ls.n), 1024, 0, st>>>(bits, parent, rank, block_tot, g, ls);
     k_scan_label<<<dim3(1, ls.n), 1024, 0, st>>>(block_tot, block_off, nb, n_out, ls);
-    if (runs)
-        k_ccl_relabel_words<true><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g, ls);
+    if (runs && sparse)
+        k_ccl_relabel_words<true, true><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap,
+                                                             g, ls);
+    else if (runs)
+        k_ccl_relabel_words<true, false><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap,
+                                                              g, ls);
     else if (wordwise)
-        k_ccl_relabel_words<false><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of, root_cap, g,
-                                                        ls);
+        k_ccl_relabel_words<false, false><<<bw, 256, 0, st>>>(bits, parent, rank, block_off, labels, root_of,
+                                                               root_cap, g, ls);
     else
         k_ccl_relabel<<<dim3(grid_for(words * 32, 256, cap), ls.n), 256, 0, st>>>(bits, parent, rank, block_off,
                                                                                  labels, root_of, root_cap, g, ls);
@@ -629,14 +770,15 @@ cudaError_t label_field(const uint32_t* bits_f, const Dims& g, int conn, int* pa
     LabelSlots one{};
     one.n = 1;
     one.f[0] = 0;
-    return label_run(bits_f, g, conn, one, parent, rank, block_tot, block_off, label, root_of, root_cap, n_out, st,
-                     launches);
+    return label_run(bits_f, g, conn, one, parent, rank, block_tot, block_off, label, root_of, root_cap, n_out, false,
+                     st, launches);
 }
 
 cudaError_t label_fields(const uint32_t* bits, const Dims& g, int conn, const LabelSlots& ls, int* parent, int* rank,
                          int* block_tot, int* block_off, int* labels, int* n_out, cudaStream_t st,
                          long long* launches) {
-    return label_run(bits, g, conn, ls, parent, rank, block_tot, block_off, labels, nullptr, 0, n_out, st, launches);
+    return label_run(bits, g, conn, ls, parent, rank, block_tot, block_off, labels, nullptr, 0, n_out, true, st,
+                     launches);
 }
 
 // --------------------------------------------------------------------------
@@ -668,27 +810,34 @@ __global__ void k_pairs(const uint32_t* __restrict__ ncmap, const uint32_t* __re
     const uint32_t* ncmap_f = ncmap + (size_t)f * words;
     const uint32_t* bits_f = bits + (size_t)f * words;
     const int* label_f = labels + (size_t)f * g.N;
+    // offsets of at most w stay within one period of the grid when w < n
+    const bool near = w < g.nx && w < g.ny && w < g.nz;
+    auto wr = [near](int v, int n) { return near ? wrap1(v, n) : wrapi(v, n); };
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < words;
          idx += (long long)gridDim.x * blockDim.x) {
         uint32_t m = ncmap_f[idx];
         if (!m) continue;
-        int row = (int)(idx / g.W), wi = (int)(idx - (long long)row * g.W);
-        int j = row % g.ny, k = row / g.ny;
+        const int row = (int)idx / g.W, wi = (int)idx - row * g.W;
+        const int j = row % g.ny, k = row / g.ny;
         while (m) {
-            int b = __ffs(m) - 1;
+            const int b = __ffs(m) - 1;
             m &= m - 1u;
-            int i = wi * 32 + b;
-            for (int dz = 0; dz <= w; ++dz)
-                for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy)
+            const int i = wi * 32 + b;
+            for (int dz = 0; dz <= w; ++dz) {
+                const int ka = wr(k + dz, g.nz), kb = wr(k - dz, g.nz);
+                for (int dy = (dz == 0 ? 0 : -w); dy <= w; ++dy) {
+                    const int ja = wr(j + dy, g.ny), jb = wr(j - dy, g.ny);
+                    const int ra = ka * g.ny + ja, rb = kb * g.ny + jb;
                     for (int dx = ((dz == 0 && dy == 0) ? 1 : -w); dx <= w; ++dx) {
-                        int ia = wrapi(i + dx, g.nx), ja = wrapi(j + dy, g.ny), ka = wrapi(k + dz, g.nz);
-                        int ib = wrapi(i - dx, g.nx), jb = wrapi(j - dy, g.ny), kb = wrapi(k - dz, g.nz);
-                        if (!bit_at(bits_f, g.W, ka * g.ny + ja, ia)) continue;
-                        if (!bit_at(bits_f, g.W, kb * g.ny + jb, ib)) continue;
-                        int la = label_f[cell(ia, ja, ka, g)], lb = label_f[cell(ib, jb, kb, g)];
+                        const int ia = wr(i + dx, g.nx), ib = wr(i - dx, g.nx);
+                        if (!bit_at(bits_f, g.W, ra, ia)) continue;
+                        if (!bit_at(bits_f, g.W, rb, ib)) continue;
+                        const int la = label_f[(size_t)ra * g.nx + ia], lb = label_f[(size_t)rb * g.nx + ib];
                         if (la == lb) continue;
                         set_insert(table, mask, pair_key(f, la < lb ? la : lb, la < lb ? lb : la), overflow);
                     }
+                }
+            }
         }
     }
 }
