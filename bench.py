@@ -504,6 +504,18 @@ def run_ours(args, rank, world):
     ms_max, updates_all = scaling.aggregate(ms, updates, device=dev)
     value = updates_all / (ms_max * 1e-3)
 
+    # drop statistics (Section 3, Appendix A) of the state the timed steps
+    # left, one event per rank, reduced over every rank's box
+    stats = None
+    try:
+        st_ = ctx.vof_stats(reset=True, histograms=True)
+        g_ = scaling.reduce_stats(st_, float(N) * cfg.h ** 3, device=dev)
+        stats = {k: g_[k] for k in ("n_drops", "d", "n_p", "volume", "events", "chi_mean", "chi_max")}
+        stats["A_zz"] = float(g_["A"][2, 2])
+        stats["ranks"] = world
+    except Exception as ex:  # reported, not fatal to the headline line
+        stats = {"error": str(ex)[:200]}
+
     # the surface-tension source of the state the timed steps left (curvature
     # of every active field by height functions, then f = sum_i gamma kappa_i
     # grad C_i on the faces): algorithmic bytes = read c and write kappa per
@@ -615,7 +627,7 @@ def run_ours(args, rank, world):
     batched = None
     if not args.no_batched and prec == vof.VOF_MIXED_LEARNED:
         try:
-            batched = batched_measure(vof, torch, dev, wts, 5, 2, 2, seed=5 + rank, n_boxes=args.boxes)
+            batched = batched_measure(vof, torch, dev, wts, 5, 2, 2, n_boxes=args.boxes, rank=rank, world=world)
         except Exception as ex:  # reported, not fatal to the headline line
             batched = {"error": str(ex)[:200]}
 
@@ -673,6 +685,7 @@ def run_ours(args, rank, world):
                        "normals": "learned (MLP 27-64-64-3, BF16 tcgen05, MYC fallback tol 1e-3)"
                        if prec == vof.VOF_MIXED_LEARNED else "MYC",
                        "faces_network": rep.get("faces_network"), "faces_myc": rep.get("faces_myc"),
+                       "faces_myc_judged": rep.get("faces_myc_judged"),
                        "training": train,
                        "step_bytes_min": step_bytes(N, rep["field_steps"] / max(args.steps, 1), es),
                        "l2": "inputs larger than L2 (fields "
@@ -682,7 +695,7 @@ def run_ours(args, rank, world):
                        "near_contact_steps": rep["near_contact_steps"]},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "roofline_update_pass": roof_update, "roofline_alu": roof_alu, "roofline_tensor": roof_tc,
-            "cpu_baseline": cpu, "fp64_path": fp64, "error_vs_fp64": err, "curvature": st_extra,
+            "cpu_baseline": cpu, "fp64_path": fp64, "error_vs_fp64": err, "curvature": st_extra, "drop_stats": stats,
             "batched": batched,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
     if fp64:
@@ -694,15 +707,19 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
-def batched_measure(vof, torch, dev, wts, steps, warmup, fp64_steps, seed=5, n_boxes=64):
-    """64 independent boxes (edges from {32,48,64,96,128}, phi 0.05-0.3, K
-    2-8) advanced as one batch: FP32 + learned normal, then plain FP64 on
-    the same boxes; each with its HBM roofline on the method's own bytes
-    (read and write c once per cell-field, the velocity once per cell, per
-    step)."""
-    from paper_2407_07463_gb300 import synth
+def batched_measure(vof, torch, dev, wts, steps, warmup, fp64_steps, seed=5, n_boxes=64, rank=0, world=1):
+    """n_boxes independent boxes per GPU (edges from {32,48,64,96,128}, phi
+    0.05-0.3, K 2-8) advanced as one batch: FP32 + learned normal, then
+    plain FP64 on the same boxes; each with its HBM roofline on the method's
+    own bytes (read and write c once per cell-field, the velocity once per
+    cell, per step).  With several ranks the job is world * n_boxes boxes,
+    split over the ranks by their n^3 K cost (longest first, to the least
+    loaded rank); the time is the slowest rank's, the work the sum."""
+    from paper_2407_07463_gb300 import scaling, synth
 
-    ws = synth.config_batched(seed=seed, n_boxes=n_boxes)
+    n_all = n_boxes * world
+    mine = scaling.partition(scaling.box_costs(synth.batched_specs(seed, n_all)), world)[rank]
+    ws = synth.config_batched(seed=seed, n_boxes=n_all, select=set(mine))
     hbm, peak_src = peaks()
     res = {}
     for prec, name in ((vof.VOF_MIXED_LEARNED, "learned"), (vof.VOF_FP64, "fp64")):
@@ -722,12 +739,13 @@ def batched_measure(vof, torch, dev, wts, steps, warmup, fp64_steps, seed=5, n_b
         B.step(n_st)
         e1.record(st)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
         rep = B.report()
         alg = sum(int(np.prod(w.shape)) * (w.k_active * 2 * es_ + 3 * es_) for w in ws)
+        ms, units = scaling.aggregate(e0.elapsed_time(e1), rep["cell_fields_per_step"] * n_st, device=dev)
+        _, alg = scaling.aggregate(0.0, alg, device=dev)
         ach = alg / (ms / n_st * 1e-3) / 1e9
-        res[name] = {"value": rep["cell_fields_per_step"] * n_st / (ms * 1e-3), "ms_per_step": ms / n_st,
-                     "steps": n_st, "cell_fields_per_step": rep["cell_fields_per_step"],
+        res[name] = {"value": units / (ms * 1e-3), "ms_per_step": ms / n_st,
+                     "steps": n_st, "cell_fields_per_step": units / n_st,
                      "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                                   "algorithmic_bytes_per_step": alg, "peak_source": peak_src},
                      "update_launch_shape": [rep["update_warps"], rep["update_blocks_per_sm"]],
@@ -736,7 +754,8 @@ def batched_measure(vof, torch, dev, wts, steps, warmup, fp64_steps, seed=5, n_b
         del cs, us
         torch.cuda.empty_cache()
     res["over_fp64"] = res["learned"]["value"] / res["fp64"]["value"]
-    res["workload"] = (f"{len(ws)} tri-periodic boxes, edges {sorted(set(w.shape[0] for w in ws))}, phi 0.05-0.3, "
+    res["workload"] = (f"{n_all} tri-periodic boxes ({len(ws)} on rank {rank} of {world}), edges "
+                       f"{sorted(set(w.shape[0] for w in ws))}, phi 0.05-0.3, "
                        f"K 2-8 (raised to the colouring's need), spheres r=4 (edge<64) / 8, 16-mode velocity amp 0.5 "
                        f"+ drift 1, CFL 0.3, no recolouring")
     return res
@@ -752,8 +771,8 @@ def run_batched(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wts, train = train_network(vof, torch, dev, args)
-    r = batched_measure(vof, torch, dev, wts, args.steps, args.warmup, args.fp64_steps, seed=5 + rank,
-                        n_boxes=args.boxes)
+    r = batched_measure(vof, torch, dev, wts, args.steps, args.warmup, args.fp64_steps, n_boxes=args.boxes,
+                        rank=rank, world=world)
     lv = r["learned"]
     line = {"metric": "VoF cell-field updates/s, 64 batched boxes; FP32+learned vs plain FP64 same GPU",
             "value": lv["value"], "unit": UNIT, "n_gpus": world, "steps": lv["steps"], "warmup": args.warmup,

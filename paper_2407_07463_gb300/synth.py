@@ -379,18 +379,30 @@ def config_large(seed=3, k_capacity=8):
                          steps=100, seed=seed)
 
 
-def config_batched(seed=5, n_boxes=64, sizes=(32, 48, 64, 96, 128)):
+def batched_specs(seed=5, n_boxes=64, sizes=(32, 48, 64, 96, 128)):
+    """(edge n, phi, K drawn) of each box of the batched workload, in order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_boxes):
+        n = int(rng.choice(sizes))
+        phi = float(rng.uniform(0.05, 0.3))
+        k = int(rng.integers(2, 9))
+        out.append((n, phi, k))
+    return out
+
+
+def config_batched(seed=5, n_boxes=64, sizes=(32, 48, 64, 96, 128), select=None):
     """Independent tri-periodic boxes: edge drawn from ``sizes``, phi uniform
     in [0.05, 0.3], K uniform in [2, 8] (raised to the number of fields the
     initial colouring needs), spheres of radius 4 cells in boxes under 64
     cells and 8 cells otherwise, 16-mode solenoidal velocity of amplitude 0.5
-    plus a vertical drift of 1, CFL 0.3.  Returns a list of Workloads."""
-    rng = np.random.default_rng(seed)
+    plus a vertical drift of 1, CFL 0.3.  Returns a list of Workloads: every
+    box, or the boxes whose indices are in ``select`` (each box is the same
+    whichever others are built)."""
     out = []
-    for b in range(n_boxes):
-        n = int(rng.choice(sizes))
-        phi = float(rng.uniform(0.05, 0.3))
-        k = int(rng.integers(2, 9))
+    for b, (n, phi, k) in enumerate(batched_specs(seed, n_boxes, sizes)):
+        if select is not None and b not in select:
+            continue
         r = 4.0 if n < 64 else 8.0
         shape = (n, n, n)
         ns = n_spheres_for_phi(shape, r, phi)
