@@ -304,7 +304,29 @@ __device__ __forceinline__ const uint32_t* slot_bits(const uint32_t* bits, const
 }
 __host__ __device__ __forceinline__ int label_blocks(const Dims& g) { return (g.N + 1023) / 1024; }
 
-__global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits, int* __restrict__ parent, Dims g, const __grid_constant__ LabelSlots ls) {
+// Heads of the runs of a row word w: the run starts, plus bit 0 where a run
+// continues from the row's previous word (carry: that word's last bit).
+__device__ __forceinline__ uint32_t run_starts(uint32_t w, uint32_t carry) { return w & ~((w << 1) | carry); }
+__device__ __forceinline__ uint32_t run_heads(uint32_t w, uint32_t carry) { return run_starts(w, carry) | (w & carry); }
+// The head of the run holding bit b of a word with heads h.
+__device__ __forceinline__ int head_of(uint32_t h, int b) {
+    return 31 - __clz(h & (b == 31 ? 0xffffffffu : ((2u << b) - 1u)));
+}
+
+// Heads of the runs of word wi of a row (cells of whole words) whose word
+// is w: the carry is the previous word's last bit.
+__device__ __forceinline__ uint32_t word_heads(const uint32_t* row_bits, int wi, uint32_t w) {
+    return run_heads(w, wi > 0 ? (row_bits[wi - 1] >> 31) : 0u);
+}
+
+// HEADS (rows of whole words): only the heads of runs get a link -- a run
+// start links to itself, and a run continuing from the previous word links
+// its bit 0 to the head of that word's last run; the other cells are never
+// read.  Otherwise every occupied cell links to its run's start (or to the
+// previous word's last cell).
+template <bool HEADS>
+__global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits, int* __restrict__ parent, Dims g,
+                                const __grid_constant__ LabelSlots ls) {
     const uint32_t* bits_f = slot_bits(bits, ls, g);
     parent += (size_t)blockIdx.y * g.N;
     const long long words = (long long)g.rows * g.W;
@@ -316,6 +338,17 @@ __global__ void k_ccl_init_runs(const uint32_t* __restrict__ bits, int* __restri
         const uint32_t carry = wi > 0 ? (bits_f[gw - 1] >> 31) : 0u;
         const uint32_t starts = w & ~((w << 1) | carry);
         const int x0 = row * g.nx + wi * 32;
+        if (HEADS) {
+            uint32_t m = starts;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1u;
+                parent[x0 + b] = x0 + b;
+            }
+            if (w & carry)
+                parent[x0] = x0 - 32 + head_of(word_heads(bits_f + (size_t)row * g.W, wi - 1, bits_f[gw - 1]), 31);
+            continue;
+        }
         uint32_t m = w;
         while (m) {
             const int b = __ffs(m) - 1;
@@ -337,7 +370,11 @@ __device__ __forceinline__ void join_rows(int* parent, uint32_t w, uint32_t wn, 
     }
 }
 
-__global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits, int* parent, Dims g, const __grid_constant__ LabelSlots ls) {
+// HEADS: the unions join the heads of the runs holding the overlap's first
+// cell in either row.
+template <bool HEADS>
+__global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits, int* parent, Dims g,
+                                 const __grid_constant__ LabelSlots ls) {
     const uint32_t* bits_f = slot_bits(bits, ls, g);
     parent += (size_t)blockIdx.y * g.N;
     const long long words = (long long)g.rows * g.W;
@@ -348,17 +385,38 @@ __global__ void k_ccl_merge_runs(const uint32_t* __restrict__ bits, int* parent,
         const int row = (int)gw / g.W, wi = (int)gw - row * g.W;
         const int j = row % g.ny, k = row / g.ny;
         const int x0 = row * g.nx + wi * 32;
+        const uint32_t* rb = bits_f + (size_t)row * g.W;
+        const uint32_t hw = HEADS ? word_heads(rb, wi, w) : 0u;
         if (wi == 0 && (w & 1u) && g.nx > 1) {
             const int last = g.nx - 1;
-            if ((bits_f[(size_t)row * g.W + (last >> 5)] >> (last & 31)) & 1u) unite(parent, x0, x0 + last);
+            const uint32_t wl = rb[last >> 5];
+            if ((wl >> (last & 31)) & 1u) {
+                const int xl = HEADS ? row * g.nx + (last & ~31) + head_of(word_heads(rb, last >> 5, wl), last & 31)
+                                     : x0 + last;
+                unite(parent, x0, xl);
+            }
         }
         const int rows_nb[2] = {k * g.ny + (j == 0 ? g.ny - 1 : j - 1), (k == 0 ? g.nz - 1 : k - 1) * g.ny + j};
         for (int q = 0; q < 2; ++q) {
             const int rn = rows_nb[q];
             if (rn == row) continue;
             const size_t gn = (size_t)rn * g.W + wi;
+            const uint32_t wn = bits_f[gn];
             const uint32_t carry = wi > 0 ? ((bits_f[gw - 1] & bits_f[gn - 1]) >> 31) : 0u;
-            join_rows(parent, w, bits_f[gn], carry, x0, rn * g.nx + wi * 32);
+            if (!HEADS) {
+                join_rows(parent, w, wn, carry, x0, rn * g.nx + wi * 32);
+                continue;
+            }
+            const uint32_t ov = w & wn;
+            uint32_t seg = ov & ~((ov << 1) | carry);
+            if (!seg) continue;
+            const uint32_t hn = word_heads(bits_f + (size_t)rn * g.W, wi, wn);
+            const int xn0 = rn * g.nx + wi * 32;
+            while (seg) {
+                const int b = __ffs(seg) - 1;
+                seg &= seg - 1u;
+                unite(parent, x0 + head_of(hw, b), xn0 + head_of(hn, b));
+            }
         }
     }
 }
@@ -407,15 +465,6 @@ __global__ void k_ccl_flatten(const uint32_t* __restrict__ bits, int* parent, Di
             parent[x0 + b] = find_root(parent, x0 + b);
         }
     }
-}
-
-// Heads of the runs of a row word w: the run starts, plus bit 0 where a run
-// continues from the row's previous word (carry: that word's last bit).
-__device__ __forceinline__ uint32_t run_starts(uint32_t w, uint32_t carry) { return w & ~((w << 1) | carry); }
-__device__ __forceinline__ uint32_t run_heads(uint32_t w, uint32_t carry) { return run_starts(w, carry) | (w & carry); }
-// The head of the run holding bit b of a word with heads h.
-__device__ __forceinline__ int head_of(uint32_t h, int b) {
-    return 31 - __clz(h & (b == 31 ? 0xffffffffu : ((2u << b) - 1u)));
 }
 
 // Flattening for the run-based links of 6-connectivity: only the head of
@@ -725,17 +774,23 @@ static cudaError_t label_run(const uint32_t* bits, const Dims& g, int conn, cons
     // the slots share the blocks a single field would get
     const int cap = std::max(1, sm_count() * 32 / ls.n);
     const dim3 bw(grid_for(words, 256, cap), ls.n), bc(grid_for(g.N, 256, cap), ls.n);
+    // rows of whole words (and a 16-byte-aligned label array): word-wise
+    // passes; with 6-connectivity there the union-find links only the heads
+    // of runs, and only they are flattened
+    const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)labels & 15) == 0;
+    const bool runs = wordwise && conn == 6;
     if (conn == 6) {
-        k_ccl_init_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
-        k_ccl_merge_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
+        if (runs) {
+            k_ccl_init_runs<true><<<bw, 256, 0, st>>>(bits, parent, g, ls);
+            k_ccl_merge_runs<true><<<bw, 256, 0, st>>>(bits, parent, g, ls);
+        } else {
+            k_ccl_init_runs<false><<<bw, 256, 0, st>>>(bits, parent, g, ls);
+            k_ccl_merge_runs<false><<<bw, 256, 0, st>>>(bits, parent, g, ls);
+        }
     } else {
         k_ccl_init<<<bc, 256, 0, st>>>(bits, parent, g, ls);
         k_ccl_merge26<<<bc, 256, 0, st>>>(bits, parent, g, ls);
     }
-    // rows of whole words (and a 16-byte-aligned label array): word-wise
-    // passes; with run-based links only the heads of runs are flattened
-    const bool wordwise = (g.nx & 31) == 0 && ((uintptr_t)labels & 15) == 0;
-    const bool runs = wordwise && conn == 6;
     if (runs)
         k_ccl_flatten_runs<<<bw, 256, 0, st>>>(bits, parent, g, ls);
     else
