@@ -21,7 +21,11 @@
 // (its stencil kept in registers) moved 0.16 ms per sweep out of the judge
 // and added 0.22 ms to the network; stopping MYC's residual once it
 // reaches the network's saved nothing (the warp runs to its slowest lane)
-// and cost 4%.
+// and cost 4%; splitting the tiles in two, the second half's normals and
+// fluxes on a second stream beside the first half's fluxes (the judge's
+// grid cut to leave a network CTA room on every SM), ran 18-29% slower
+// than the pair in turn (the two kernels did not overlap usefully, and the
+// judge lost the occupancy it needs).
 #include "boxes.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"
