@@ -24,9 +24,12 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 // holding the centre cell's volume fraction, extended over the 3x3x3 block;
 // the mean over the 27 cells of |predicted - actual| fraction, with that
 // plane's constant (FP32).  The reflection and ordering of the normal
-// and the constants of its volume are taken once per stencil; the cells
-// the plane leaves whole cost a compare, the cut ones the piecewise closed
-// form (vol_pw).  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
+// and the constants of its volume are taken once per stencil; every cell
+// then takes the piecewise closed form (vol_pw, which returns 0 or 1 for a
+// cell the plane leaves whole) in one unrolled, branch-free pass -- a first
+// pass that settled the whole cells by a compare and a loop over the cut
+// ones cost 27% more instructions, the loop running to the largest cut
+// count of the warp.  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
 // column of a shared-memory tile).
 struct Residual {
     float e;      // mean |predicted - actual| over the 27 cells
@@ -41,26 +44,11 @@ static __device__ __noinline__ Residual normal_residual_m(const float* st, float
     const VolPW p = vol_pw_make(a, b, c);
     // the plane constant in the reflected frame, and in the grid's
     const float A = alpha_pw(p, st[13 * STRIDE]);
-    // first pass: the cells the plane leaves whole (volume 0 or 1) cost a
-    // compare; the cut ones are collected in a mask and take the volume in a
-    // second pass (about a third of the 27 for a plane through the centre)
     float e = 0.f;
-    uint32_t cut = 0u;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
         const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float aq = A - (m0 * i + m1 * j + m2 * k);
-        if (aq > 0.f && aq < p.S)
-            cut |= 1u << q;
-        else
-            e += fabsf((aq <= 0.f ? 0.f : 1.f) - st[q * STRIDE]);
-    }
-    while (cut) {
-        const int q = __ffs(cut) - 1;
-        cut &= cut - 1u;
-        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        const float v = vol_pw(p, A - (m0 * i + m1 * j + m2 * k));
-        e += fabsf(v - st[q * STRIDE]);
+        e += fabsf(vol_pw(p, A - (m0 * i + m1 * j + m2 * k)) - st[q * STRIDE]);
     }
     return {e * (1.f / 27.f), A - off};
 }
