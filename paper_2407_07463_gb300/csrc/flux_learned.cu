@@ -25,7 +25,9 @@
 // fluxes on a second stream beside the first half's fluxes (the judge's
 // grid cut to leave a network CTA room on every SM), ran 18-29% slower
 // than the pair in turn (the two kernels did not overlap usefully, and the
-// judge lost the occupancy it needs).
+// judge lost the occupancy it needs); letting every thread of a tile whose
+// faces all need MYC take its own face's MYC normal and residual (no
+// compaction, two barriers fewer) ran 4% slower.
 #include "boxes.cuh"
 #include "mlp.cuh"
 #include "mlp_tile.cuh"

@@ -26,10 +26,10 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 // plane's constant (FP32).  The reflection and ordering of the normal
 // and the constants of its volume are taken once per stencil; every cell
 // then takes the piecewise closed form (vol_pw, which returns 0 or 1 for a
-// cell the plane leaves whole) in one unrolled, branch-free pass -- a first
-// pass that settled the whole cells by a compare and a loop over the cut
-// ones cost 27% more instructions, the loop running to the largest cut
-// count of the warp.  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
+// cell the plane leaves whole) in one branch-free pass -- a first pass
+// that settled the whole cells by a compare and a loop over the cut ones
+// cost 27% more instructions, the loop running to the largest cut count of
+// the warp.  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
 // column of a shared-memory tile).
 struct Residual {
     float e;      // mean |predicted - actual| over the 27 cells
@@ -45,10 +45,17 @@ static __device__ __noinline__ Residual normal_residual_m(const float* st, float
     // the plane constant in the reflected frame, and in the grid's
     const float A = alpha_pw(p, st[13 * STRIDE]);
     float e = 0.f;
+    // one rolled loop over the three planes along z keeps the code small
+    // enough for the instruction cache; each plane's 9 cells are unrolled
+#pragma unroll 1
+    for (int k = -1; k <= 1; ++k) {
+        const float* sk = st + (k + 1) * 9 * STRIDE;
+        const float mk = m2 * (float)k;
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const int i = q % 3 - 1, j = (q / 3) % 3 - 1, k = q / 9 - 1;
-        e += fabsf(vol_pw(p, A - (m0 * i + m1 * j + m2 * k)) - st[q * STRIDE]);
+        for (int q = 0; q < 9; ++q) {
+            const int i = q % 3 - 1, j = q / 3 - 1;
+            e += fabsf(vol_pw(p, A - (m0 * i + m1 * j + mk)) - sk[q * STRIDE]);
+        }
     }
     return {e * (1.f / 27.f), A - off};
 }
