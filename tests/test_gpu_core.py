@@ -369,6 +369,66 @@ def test_recolour_bit_exact(vof, seed):
     ctx.close()
 
 
+# Rows of 1, 2, 4 and 8 whole words, with partial tiles along y and z: the
+# shared-memory tiles of Step 1 (256 / W rows a block, a halo of w rows).
+TILED_SHAPES = [(20, 18, 32), (20, 13, 64), (12, 11, 128), (12, 9, 256)]
+
+
+@pytest.mark.parametrize("shape", TILED_SHAPES)
+@pytest.mark.parametrize("w", [1, 2, 3])
+def test_near_contact_flags_tiled(vof, shape, w):
+    """Step 1 on rows of whole words (the tiled kernel where the tile and its
+    halo fit the grid) equals the oracle field by field."""
+    rng = np.random.default_rng(sum(shape) * 10 + w)
+    K = 10
+    dens = np.array([0.0, 0.0001, 0.0003, 0.001, 0.05] + [0.0] * 5)[:, None, None, None]
+    c = rng.random((K,) + shape) * (rng.random((K,) + shape) < dens)
+    nz, ny, nx = shape
+    # one pair per field around an empty middle cell: across a tile's edge
+    # in y, across the periodic ends in y, z and x; then a pair three cells
+    # apart (no middle cell)
+    j1 = min(15, ny - 3)
+    c[5, 8, j1, 31], c[5, 8, j1 + 2, 31] = 0.7, 0.6
+    c[6, 0, ny - 1, 5], c[6, 0, 1, 5] = 0.5, 0.9
+    c[7, nz - 1, 3, 9], c[7, 1, 3, 9] = 0.8, 0.4
+    c[8, 2, 4, nx - 1], c[8, 2, 4, 1] = 0.6, 0.6
+    c[9, 4, 6, 30], c[9, 4, 6, 33 % nx] = 0.9, 0.9
+    ctx, c_d, _, _ = run_gpu(vof, c, np.zeros((3,) + shape), 0.0, 0, stencil_w=w)
+    flags = ctx.vof_near_contact()
+    for f in range(K):
+        assert bool(flags[f]) == O.near_contact(c[f], w), f
+    ctx.close()
+
+
+def cubes_in_fields(rng, shape, K, k_active, n, size=3):
+    """n cubes of random fractions spread over the first k_active fields."""
+    c = np.zeros((K,) + shape)
+    for q in range(n):
+        lo = [int(rng.integers(0, s)) for s in shape]
+        sl = tuple(np.arange(l, l + size) % s for l, s in zip(lo, shape))
+        c[q % k_active][np.ix_(*sl)] = rng.uniform(0.3, 1.0)
+    return c
+
+
+@pytest.mark.parametrize("shape,n,k_active", [((20, 18, 32), 40, 1), ((16, 12, 64), 40, 2),
+                                              ((12, 11, 128), 60, 3), ((10, 12, 256), 80, 3)])
+def test_recolour_bit_exact_whole_word_rows(vof, shape, n, k_active):
+    """Steps 1-4 where the rows are whole words: tiled Step 1, every flagged
+    field tagged in one chain (run-head links, tags written only where a
+    word is occupied), pairs, the dilated touch test and the move -- the
+    fields after the call equal the oracle's bit for bit."""
+    rng = np.random.default_rng(sum(shape) + n)
+    K = 8
+    c = cubes_in_fields(rng, shape, K, k_active, n)
+    want, na_o, nm_o, st_o, _ = O.recolour(c, k_active)
+    ctx, c_d, _, _ = run_gpu(vof, c, np.zeros((3,) + shape), 0.0, 0, k_active=k_active)
+    moved, na, st = ctx.vof_recolour()
+    assert (moved, na, st) == (nm_o, na_o, st_o)
+    assert moved > 0
+    assert np.array_equal(c_d.cpu().numpy(), want)
+    ctx.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_recolour_with_threshold(vof, precision):
     """tau = 1e-6: round-off residues below tau are not drops; the float path
