@@ -14,4 +14,8 @@ int update_occupancy(bool fp64, int warps) {
 cudaError_t advect_first_sweep_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a) {
     return advect_first_sweep(S, a);
 }
+cudaError_t patch_list_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int d, const uint32_t* bits, const int* labels,
+                          const MoveTables& mt, const int* target) {
+    return patch_list_set(S, a, d, bits, labels, mt, target);
+}
 }  // namespace vof

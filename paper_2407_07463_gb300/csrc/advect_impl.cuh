@@ -395,6 +395,23 @@ cudaError_t advect_set(const BoxSet<T, NB>& S, SweepArgs& a, int nsteps) {
     return cudaGetLastError();
 }
 
+// The current face list after Step 4 moved drops of a single box: faces
+// whose donor moved change field (k_list_patch); d is the direction of the
+// sweep the list serves.  The list geometry is the one advect_set used.
+template <typename T>
+cudaError_t patch_list_set(const BoxSet<T, 1>& S, SweepArgs& a, int d, const uint32_t* bits, const int* labels,
+                           const MoveTables& mt, const int* target) {
+    if (!a.list_valid) return cudaSuccess;
+    const bool vec = rows_vectorisable<T>(S.b[0].g);
+    const SweepGrid G = sweep_grid(S, vec, a);
+    unsigned long long* list = a.list + (a.list_cur ? a.list_entries : 0);
+    const int* counts = a.counts + (a.list_cur ? kSweepBlocks : 0);
+    k_list_patch<T><<<std::min(G.gb, sm_count() * 8), 256, 0, a.stream>>>(S, d, list, G.cap, counts, G.gb, bits,
+                                                                         labels, mt, target);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
 // Listing from c and the first sweep of step a.step only (c -> first
 // scratch buffer; c itself is not modified): a representative, repeatable
 // unit of work for timing launch shapes.

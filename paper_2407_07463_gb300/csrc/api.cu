@@ -240,8 +240,42 @@ vof_status scan_velocity(vof_ctx* ctx) {
     return VOF_OK;
 }
 
-// Steps 1-4 on the current state (see vof_recolour).
-vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
+// The context's state as a one-box set.
+template <typename T>
+static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
+    BoxSet<T, 1> S;
+    BoxDev<T>& B = S.b[0];
+    const Dims& g = ctx->g;
+    const int CH = 32 * VecOf<T>::W;
+    B.g = g;
+    B.K = ctx->n_active;
+    B.item0 = 0;
+    B.chunk0 = 0;
+    B.cpr = (g.nx + CH - 1) / CH;
+    B.divK = fastdiv_make((uint32_t)B.K);
+    B.divcpr = fastdiv_make((uint32_t)B.cpr);
+    B.divny = fastdiv_make((uint32_t)g.ny);
+    B.sfac = (T)(dt / ctx->cfg.h);
+    B.c = (T*)ctx->c;
+    B.b1 = ctx->slot<T>(S_BUF1);
+    B.b2 = ctx->slot<T>(S_BUF2);
+    B.flux = ctx->slot<T>(S_FLUX);
+    B.u = (const T*)ctx->u;
+    B.net = ctx->cfg.precision == VOF_MIXED_LEARNED ? ctx->slot<float4>(S_NET) : nullptr;
+    B.ccbits = ctx->slot<uint32_t>(S_CCBITS);
+    B.occbits = ctx->slot<uint32_t>(S_BITS);
+    B.clipped = clipped;
+    S.n = 1;
+    S.items = B.K * g.rows * B.cpr;
+    S.chunks = g.rows * B.cpr;
+    return S;
+}
+
+// Steps 1-4 on the current state (see vof_recolour).  patch (inside
+// vof_step): the sweep arguments whose current face list is rewritten for
+// the moved drops instead of being listed again.
+vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out, SweepArgs* patch = nullptr,
+                         double dt = 0.0) {
     const Dims& g = ctx->g;
     const vof_config& cf = ctx->cfg;
     cudaStream_t st = ctx->stream;
@@ -409,6 +443,21 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out) {
                                      (int)hfields.size(), d_target, st);
              }));
     ctx->launches += 1;
+    if (patch && moved > 0 && ctx->n_active != na0) {
+        // a newly activated field changes the list's segment geometry (its
+        // capacity per segment grows with the fields): list again
+        patch->list_valid = false;
+    } else if (patch && moved > 0) {
+        // the list serves the first sweep of the next step
+        double* clipped = (double*)(ctx->misc() + kMiscClipped);
+        const int d = (int)(ctx->step % 3);
+        VOF_CUDA(ctx, timed(ctx, P_FIND_FACES, [&] {
+                     return ctx->fp64 ? patch_list_fp64(ctx_box_set<double>(ctx, clipped, dt), *patch, d, bits, labels,
+                                                        mt, d_target)
+                                      : patch_list_fp32(ctx_box_set<float>(ctx, clipped, dt), *patch, d, bits, labels,
+                                                        mt, d_target);
+                 }));
+    }
     ctx->bits_valid = false;
     VOF_CUDA(ctx, cudaStreamSynchronize(st));
     *moved_out = moved;
@@ -559,37 +608,6 @@ vof_status vof_set_velocity(vof_ctx* ctx, const void* u_dev) {
 
 }  // extern "C"
 
-// The context's state as a one-box set.
-template <typename T>
-static BoxSet<T, 1> ctx_box_set(vof_ctx* ctx, double* clipped, double dt) {
-    BoxSet<T, 1> S;
-    BoxDev<T>& B = S.b[0];
-    const Dims& g = ctx->g;
-    const int CH = 32 * VecOf<T>::W;
-    B.g = g;
-    B.K = ctx->n_active;
-    B.item0 = 0;
-    B.chunk0 = 0;
-    B.cpr = (g.nx + CH - 1) / CH;
-    B.divK = fastdiv_make((uint32_t)B.K);
-    B.divcpr = fastdiv_make((uint32_t)B.cpr);
-    B.divny = fastdiv_make((uint32_t)g.ny);
-    B.sfac = (T)(dt / ctx->cfg.h);
-    B.c = (T*)ctx->c;
-    B.b1 = ctx->slot<T>(S_BUF1);
-    B.b2 = ctx->slot<T>(S_BUF2);
-    B.flux = ctx->slot<T>(S_FLUX);
-    B.u = (const T*)ctx->u;
-    B.net = ctx->cfg.precision == VOF_MIXED_LEARNED ? ctx->slot<float4>(S_NET) : nullptr;
-    B.ccbits = ctx->slot<uint32_t>(S_CCBITS);
-    B.occbits = ctx->slot<uint32_t>(S_BITS);
-    B.clipped = clipped;
-    S.n = 1;
-    S.items = B.K * g.rows * B.cpr;
-    S.chunks = g.rows * B.cpr;
-    return S;
-}
-
 extern "C" {
 
 vof_status vof_set_mlp(vof_ctx* ctx, const void* weights_dev, double fallback_tol) {
@@ -656,10 +674,10 @@ vof_status vof_step(vof_ctx* ctx, double dt, int32_t nsteps, vof_step_report* re
         ctx->step += n;
         if (ctx->cfg.recolour) {
             int moved = 0, fired = 0;
-            vof_status r = recolour_impl(ctx, &moved, &fired);
+            // the face list of the next sweep is patched for moved drops
+            vof_status r = recolour_impl(ctx, &moved, &fired, &a, dt);
             if (r != VOF_OK && r != VOF_ERR_NO_FREE_FIELD) return r;
             if (r == VOF_ERR_NO_FREE_FIELD) result = r;
-            if (moved) a.list_valid = false;  // moves change the interfacial donors
             moved_total += moved;
             fired_steps += fired;
             in_use_max = std::max(in_use_max, ctx->n_in_use);

@@ -650,6 +650,41 @@ __device__ __forceinline__ BoxFace decode_box_face(const BoxSet<T, NB>& S, unsig
     return r;
 }
 
+// After Step 4 moved drops (one box): every face of the current list (the
+// next sweep's faces, direction d, whose upwind donor is interfacial) whose
+// donor is a cell of a moving drop now belongs to the drop's target field.
+// A moved cell keeps its value and only changes field, and the target
+// field held nothing occupied within reach of the drop, so the rest of the
+// list stands (a target cell that held a residue below the occupancy
+// threshold may end up listed twice, which writes the same flux twice).  A
+// donor's tag is read only where the Step 1 snapshot marks it occupied.
+template <typename T>
+__global__ void __launch_bounds__(256) k_list_patch(const __grid_constant__ BoxSet<T, 1> S, int d,
+                                                    unsigned long long* __restrict__ list, long long cap,
+                                                    const int* __restrict__ counts, int nseg,
+                                                    const uint32_t* __restrict__ bits,
+                                                    const int* __restrict__ labels, MoveTables mt,
+                                                    const int* __restrict__ target) {
+    const Dims& g = S.b[0].g;
+    const size_t wpf = (size_t)g.rows * g.W;
+    for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+        const int n = counts[sg];
+        unsigned long long* seg = list + (size_t)sg * cap;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const unsigned long long key = seg[e];
+            const int f = (int)((key >> 54) & 15u);
+            if (mt.mv_count[f] == 0) continue;
+            T uv;
+            const BoxFace fc = decode_box_face(S, key, d, uv);
+            const size_t row = (size_t)fc.dk * g.ny + fc.dj;
+            if (!((bits[(size_t)f * wpf + row * g.W + (fc.di >> 5)] >> (fc.di & 31)) & 1u)) continue;
+            const int m = moving_index(mt, f, labels[(size_t)f * g.N + fc.donor]);
+            const int tg = m >= 0 ? target[m] : -1;
+            if (tg >= 0) seg[e] = (key & ~(15ull << 54)) | ((unsigned long long)tg << 54);
+        }
+    }
+}
+
 // MYC fluxes of the listed faces of every box (one thread per face, tiles of
 // kFaceTile consecutive entries whose first segment tile_seg gives).
 template <typename T, int NB>

@@ -62,6 +62,7 @@ cudaError_t note_cuda_error(cudaError_t e);
 const char* last_cuda_error_name();
 struct SweepArgs;
 struct MlpBlob;
+struct MoveTables;
 template <typename T, int NB>
 struct BoxSet;
 constexpr int kMaxBoxes = 64;
@@ -84,6 +85,14 @@ cudaError_t advect_set_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int nsteps
 cudaError_t advect_set_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp64(const BoxSet<double, kMaxBoxes>& S, SweepArgs& a, int nsteps);
 cudaError_t advect_set_fp32(const BoxSet<float, kMaxBoxes>& S, SweepArgs& a, int nsteps);
+// After Step 4 moved drops of a context's box: the faces of the current
+// list whose donor moved take the drop's target field (d: the direction of
+// the sweep the list serves; bits and labels: Step 1's occupancy and Step
+// 2's tags; target[m]: the field drop m moved to, or -1).
+cudaError_t patch_list_fp32(const BoxSet<float, 1>& S, SweepArgs& a, int d, const uint32_t* bits, const int* labels,
+                            const MoveTables& mt, const int* target);
+cudaError_t patch_list_fp64(const BoxSet<double, 1>& S, SweepArgs& a, int d, const uint32_t* bits, const int* labels,
+                            const MoveTables& mt, const int* target);
 // Resident blocks per SM of a batch's update pass with `warps` warps per
 // block (0 if the query fails), asked of the unit that launches it.
 int update_occupancy(bool fp64, int warps);
@@ -159,6 +168,22 @@ struct MoveTables {
     const int* mv_label;   // [M]
     int M;
 };
+
+#ifdef __CUDACC__
+// Index of label l among field f's moving drops, or -1.
+__device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) {
+    int lo = mt.mv_start[f], n = mt.mv_count[f];
+    int a = 0, b = n - 1;
+    while (a <= b) {
+        int mid = (a + b) >> 1;
+        int v = mt.mv_label[lo + mid];
+        if (v == l) return lo + mid;
+        if (v < l) a = mid + 1;
+        else b = mid - 1;
+    }
+    return -1;
+}
+#endif
 // Moving-drop bits (mvbits: a plane per field of mv_fields), then touch[m]
 // and conflict[m] for every moving drop; dil: scratch of n_active +
 // 2 n_mv_fields bit planes; reach <= 16, n_active and n_mv_fields <= 32.

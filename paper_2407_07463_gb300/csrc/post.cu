@@ -11,20 +11,6 @@ namespace vof {
 // --------------------------------------------------------------------------
 // Step 4
 
-// Index of label l among field f's moving drops, or -1.
-__device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) {
-    int lo = mt.mv_start[f], n = mt.mv_count[f];
-    int a = 0, b = n - 1;
-    while (a <= b) {
-        int mid = (a + b) >> 1;
-        int v = mt.mv_label[lo + mid];
-        if (v == l) return lo + mid;
-        if (v < l) a = mid + 1;
-        else b = mid - 1;
-    }
-    return -1;
-}
-
 // Occupancy bits of the cells of moving drops, one bit plane per field of
 // mv_fields (same row layout as the occupancy bits).  A lane takes a word:
 // only its occupied cells (the field's occupancy bits, from which its tags
