@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_dilate_rows(const uint32_t* __restrict_
 }
 
 cudaError_t dilate_planes(const uint32_t* src, uint32_t* dst, uint32_t* tmp, int n, const Dims& g, int reach,
-                                 cudaStream_t st) {
+                          cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const long long pf = (long long)g.rows * g.W;
     const dim3 grid(grid_for(pf, 256, std::max(1, sm_count() * 32 / n)), n);
@@ -201,17 +201,24 @@ __global__ void __launch_bounds__(kNcThreads) k_near_contact_tile(const uint32_t
     const uint32_t* fb = bits + (size_t)f * per_field;
     // the tile's rows and their halo (the caller ensures TY + w <= ny and
     // TZ + w <= nz, so every staged index is within one period)
+    uint32_t any = 0u;
     for (int t = threadIdx.x; t < HY * HZ * W; t += kNcThreads) {
         const int wi = t & (W - 1), r = t >> lw;
         const int hz = r / HY, hy = r - hz * HY;
         const int j = wrap1(j0 - w + hy, g.ny), k = wrap1(k0 - w + hz, g.nz);
-        s_rows[t] = fb[(size_t)(k * g.ny + j) * W + wi];
+        const uint32_t v = fb[(size_t)(k * g.ny + j) * W + wi];
+        s_rows[t] = v;
+        any |= v;
     }
-    __syncthreads();
+    const bool occupied = __syncthreads_or(any != 0u);
     const int wi = threadIdx.x & (W - 1), r = threadIdx.x >> lw;
     const int lz = r >> ty_log, ly = r - (lz << ty_log);
     const int j = j0 + ly, k = k0 + lz;
     if (j >= g.ny || k >= g.nz) return;  // a partial tile at the grid's end
+    if (!occupied) {  // tile and halo empty: nothing fires, nothing is occupied
+        if (ncmap) ncmap[(size_t)f * per_field + (size_t)(k * g.ny + j) * W + wi] = 0u;
+        return;
+    }
     const uint32_t* base = s_rows + ((size_t)(lz + w) * HY + (ly + w)) * W;
     const uint32_t centre = base[wi];
     const uint32_t empty = ~centre;
