@@ -359,19 +359,24 @@ __device__ __noinline__ T alpha_sorted(T a, T b, T c, T v, int* region = nullptr
 }
 
 // One Newton step in double on the closed form of the region the float
-// root lies in (the FP64 part of the mixed-precision plane constant).
+// root lies in (the FP64 part of the mixed-precision plane constant).  The
+// residual f and its slope are formed in double; their quotient, the step,
+// is about 1e-7 of alpha after the float root, so it is taken in float (a
+// relative error of 1e-7 in the step is 1e-14 in alpha) instead of an FP64
+// division, which GB300 issues at a small fraction of its FP32 rate.
+__device__ __forceinline__ double newton_step(double f, double fp) { return (double)((float)f / (float)fp); }
 __device__ __forceinline__ double alpha_refine_fp64(double a, double b, double c, double v, double al,
                                                     int reg) {
     if (reg == 0) {
         if (b <= 1e-30) return c * v;
-        if (al < b) return al - (al * al - 2.0 * b * c * v) / (2.0 * al);
+        if (al < b) return al - newton_step(al * al - 2.0 * b * c * v, 2.0 * al);
         return c * v + 0.5 * b;
     }
     if (reg == 5) return c * v + 0.5 * (a + b);
-    if (reg == 1) return al - (al * al * al - 6.0 * a * b * c * v) / (3.0 * al * al);
+    if (reg == 1) return al - newton_step(al * al * al - 6.0 * a * b * c * v, 3.0 * al * al);
     if (reg == 2) {
-        double f = al * al - a * al + a * a / 3.0 - 2.0 * b * c * v;
-        return al - f / (2.0 * al - a);
+        double f = al * al - a * al + a * a * (1.0 / 3.0) - 2.0 * b * c * v;
+        return al - newton_step(f, 2.0 * al - a);
     }
     double da = al - a, db = al - b, dc = al - c;
     double f = al * al * al - da * da * da - db * db * db - 6.0 * a * b * c * v;
@@ -381,7 +386,7 @@ __device__ __forceinline__ double alpha_refine_fp64(double a, double b, double c
         fp -= dc * dc;
     }
     fp *= 3.0;
-    return fp > 0.0 ? al - f / fp : al;
+    return fp > 0.0 ? al - newton_step(f, fp) : al;
 }
 
 // Plane constant alpha with plic_volume(m, alpha) = cv.
