@@ -339,16 +339,24 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out, SweepArgs
              }));
     VOF_CUDA(ctx, timed(ctx, P_PAIRS, [&] { return compact_pairs(table, kPairCap, plist, counters + 1, st); }));
     ctx->launches += 1;
+    // the pair count, the overflow flag and the first kFastPairs keys come
+    // back with one synchronisation (the rest, rarely, with a second)
+    constexpr size_t kFastPairs = 1024;
     unsigned long long npairs = 0;
     int hover = 0;
+    std::vector<unsigned long long> keys(kFastPairs);
     VOF_CUDA(ctx, cudaMemcpyAsync(&npairs, counters + 1, 8, cudaMemcpyDeviceToHost, st));
     VOF_CUDA(ctx, cudaMemcpyAsync(&hover, overflow, 4, cudaMemcpyDeviceToHost, st));
+    VOF_CUDA(ctx, cudaMemcpyAsync(keys.data(), plist, kFastPairs * 8, cudaMemcpyDeviceToHost, st));
     VOF_CUDA(ctx, cudaStreamSynchronize(st));
     if (hover) return VOF_ERR_CAPACITY;
     if (npairs == 0) return VOF_OK;
-    std::vector<unsigned long long> keys(npairs);
-    VOF_CUDA(ctx, cudaMemcpyAsync(keys.data(), plist, npairs * 8, cudaMemcpyDeviceToHost, st));
-    VOF_CUDA(ctx, cudaStreamSynchronize(st));
+    keys.resize(npairs);
+    if (npairs > kFastPairs) {
+        VOF_CUDA(ctx, cudaMemcpyAsync(keys.data() + kFastPairs, plist + kFastPairs, (npairs - kFastPairs) * 8,
+                                      cudaMemcpyDeviceToHost, st));
+        VOF_CUDA(ctx, cudaStreamSynchronize(st));
+    }
     std::sort(keys.begin(), keys.end());
 
     // moving drops per field: pairs (a < b) in order mark b unless a or b moves
@@ -459,7 +467,9 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out, SweepArgs
                  }));
     }
     ctx->bits_valid = false;
-    VOF_CUDA(ctx, cudaStreamSynchronize(st));
+    // vof_recolour returns with the work done; inside vof_step the next
+    // step's launches follow on the same stream without a wait
+    if (!patch) VOF_CUDA(ctx, cudaStreamSynchronize(st));
     *moved_out = moved;
     return status;
 }
