@@ -33,6 +33,7 @@ enum Slot {
     S_PTABLE,
     S_PLIST,
     S_MV,
+    S_MVMAP,
     S_TOUCH,
     S_CONFLICT,
     S_TARGET,
@@ -129,6 +130,7 @@ Layout layout_for(const vof_config* c) {
     L.size[S_PTABLE] = (size_t)kPairCap * 8;
     L.size[S_PLIST] = (size_t)kPairCap * 8;
     L.size[S_MV] = (size_t)(3 * kMaxK + kMoveCap) * 4;
+    L.size[S_MVMAP] = K * (size_t)kMoveMapWords * 4;
     L.size[S_TOUCH] = (size_t)kMoveCap * 4;
     L.size[S_CONFLICT] = (size_t)kMoveCap * kMoveWords * 4;
     L.size[S_TARGET] = (size_t)kMoveCap * 4;
@@ -403,7 +405,11 @@ vof_status recolour_impl(vof_ctx* ctx, int* moved_out, int* fired_out, SweepArgs
     VOF_CUDA(ctx, cudaMemcpyAsync(d_count, hcount.data(), kMaxK * 4, cudaMemcpyHostToDevice, st));
     VOF_CUDA(ctx, cudaMemcpyAsync(d_fields, hfields.data(), hfields.size() * 4, cudaMemcpyHostToDevice, st));
     VOF_CUDA(ctx, cudaMemcpyAsync(d_label, hlabel.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
-    MoveTables mt{d_start, d_count, d_label, M};
+    uint32_t* mv_map = ctx->slot<uint32_t>(S_MVMAP);
+    MoveTables mt{d_start, d_count, d_label, M, mv_map};
+    VOF_CUDA(ctx, cudaMemsetAsync(mv_map, 0, ctx->L.size[S_MVMAP], st));
+    VOF_CUDA(ctx, move_map(mt, mv_map, d_fields, (int)hfields.size(), st));
+    ctx->launches += 1;
     unsigned* touch = ctx->slot<unsigned>(S_TOUCH);
     unsigned* conflict = ctx->slot<unsigned>(S_CONFLICT);
     VOF_CUDA(ctx, cudaMemsetAsync(touch, 0, (size_t)M * 4, st));

@@ -678,7 +678,9 @@ __global__ void __launch_bounds__(256) k_list_patch(const __grid_constant__ BoxS
             const BoxFace fc = decode_box_face(S, key, d, uv);
             const size_t row = (size_t)fc.dk * g.ny + fc.dj;
             if (!((bits[(size_t)f * wpf + row * g.W + (fc.di >> 5)] >> (fc.di & 31)) & 1u)) continue;
-            const int m = moving_index(mt, f, labels[(size_t)f * g.N + fc.donor]);
+            const int l = labels[(size_t)f * g.N + fc.donor];
+            if (!is_moving(mt, f, l)) continue;
+            const int m = moving_index(mt, f, l);
             const int tg = m >= 0 ? target[m] : -1;
             if (tg >= 0) seg[e] = (key & ~(15ull << 54)) | ((unsigned long long)tg << 54);
         }

@@ -162,11 +162,16 @@ cudaError_t compact_pairs(const unsigned long long* table, int cap, unsigned lon
 
 // Step 4 helpers.  Moving drops are listed per field in increasing label
 // order: mv_label[mv_start[f] .. mv_start[f] + mv_count[f]).
+// mv_map: a bit per (field, tag) below kMoveMapTags, set for moving drops
+// (a lookup without the search); larger tags are searched.
+constexpr int kMoveMapTags = 1 << 16;
+constexpr int kMoveMapWords = kMoveMapTags / 32;  // per field
 struct MoveTables {
-    const int* mv_start;   // [K]
-    const int* mv_count;   // [K]
-    const int* mv_label;   // [M]
+    const int* mv_start;      // [K]
+    const int* mv_count;      // [K]
+    const int* mv_label;      // [M]
     int M;
+    const uint32_t* mv_map;   // [K][kMoveMapWords]
 };
 
 #ifdef __CUDACC__
@@ -183,6 +188,13 @@ __device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) 
     }
     return -1;
 }
+
+// Is tag l (> 0) of field f a moving drop?
+__device__ __forceinline__ bool is_moving(const MoveTables& mt, int f, int l) {
+    if (l <= 0) return false;
+    if (l < kMoveMapTags) return (mt.mv_map[(size_t)f * kMoveMapWords + (l >> 5)] >> (l & 31)) & 1u;
+    return moving_index(mt, f, l) >= 0;
+}
 #endif
 // Moving-drop bits (mvbits: a plane per field of mv_fields), then touch[m]
 // and conflict[m] for every moving drop; dil: scratch of n_active +
@@ -190,6 +202,9 @@ __device__ __forceinline__ int moving_index(const MoveTables& mt, int f, int l) 
 cudaError_t recolour_touch(const int* labels, const uint32_t* bits, uint32_t* mvbits, uint32_t* dil, const Dims& g,
                            int n_active, int reach, MoveTables mt, const int* mv_fields, int n_mv_fields,
                            unsigned* touch, unsigned* conflict, int Mw, cudaStream_t st, long long* launches);
+// The bit map of moving tags (mt.mv_map, cleared by the caller) for the
+// n_fields fields listed in mv_fields.
+cudaError_t move_map(MoveTables mt, uint32_t* map, const int* mv_fields, int n_fields, cudaStream_t st);
 // Moves the cells set in mvbits to their drop's target field.
 cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t* mvbits, const Dims& g,
                           MoveTables mt, const int* mv_fields, int n_mv_fields, const int* target, cudaStream_t st);

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_moving_bits(const int* __restrict__ lab
                 const int b = __ffs(occ) - 1;
                 occ &= occ - 1u;
                 const int l = lab[b];
-                if (l != 0 && moving_index(mt, f, l) >= 0) mv |= 1u << b;
+                if (is_moving(mt, f, l)) mv |= 1u << b;
             }
         }
         mvbits[wd] = mv;
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) k_touch_words(const int* __restrict__ lab
                             wv &= wv - 1ull;
                             const int y = cell(wrapi(x0 + b, g.nx), jj, kk, g);
                             const int l2 = labels[(size_t)f2 * g.N + y];
+                            if (f2 == f && l2 == mt.mv_label[m]) continue;  // the drop's own cell
                             const int m2 = moving_index(mt, f2, l2);
                             if (m2 < 0 || m2 == m) continue;
                             const unsigned bitm = 1u << (m2 & 31);
@@ -190,6 +191,22 @@ __global__ void __launch_bounds__(256) k_move(T* c, const int* __restrict__ labe
             c[(size_t)f * g.N + x] = T(0);
         }
     }
+}
+
+// One block per listed field sets the bits of its moving tags.
+__global__ void k_move_map(MoveTables mt, uint32_t* __restrict__ map, const int* __restrict__ mv_fields) {
+    const int f = mv_fields[blockIdx.x];
+    const int lo = mt.mv_start[f], n = mt.mv_count[f];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int l = mt.mv_label[lo + k];
+        if (l > 0 && l < kMoveMapTags) atomicOr(map + (size_t)f * kMoveMapWords + (l >> 5), 1u << (l & 31));
+    }
+}
+
+cudaError_t move_map(MoveTables mt, uint32_t* map, const int* mv_fields, int n_fields, cudaStream_t st) {
+    if (n_fields <= 0) return cudaSuccess;
+    k_move_map<<<n_fields, 128, 0, st>>>(mt, map, mv_fields);
+    return cudaGetLastError();
 }
 
 cudaError_t recolour_move(void* c, bool fp64, const int* labels, const uint32_t* mvbits, const Dims& g,
