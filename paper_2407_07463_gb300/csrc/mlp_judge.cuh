@@ -25,8 +25,8 @@ __device__ __forceinline__ bool l1_normalise(const float n[3], float m[3]) {
 // the mean over the 27 cells of |predicted - actual| fraction, with that
 // plane's constant (FP32).  The reflection and ordering of the normal
 // and the constants of its volume are taken once per stencil; every cell
-// then takes the piecewise closed form (vol_pw, which returns 0 or 1 for a
-// cell the plane leaves whole) in one branch-free pass -- a first pass
+// then takes the piecewise closed form (vol_pw_clamped, which gives 0 or 1
+// for a cell the plane leaves whole) in one branch-free pass -- a first pass
 // that settled the whole cells by a compare and a loop over the cut ones
 // cost 27% more instructions, the loop running to the largest cut count of
 // the warp.  The value of cell q is st[q * STRIDE] (STRIDE > 1: a
@@ -54,7 +54,7 @@ static __device__ __noinline__ Residual normal_residual_m(const float* st, float
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const int i = q % 3 - 1, j = q / 3 - 1;
-            e += fabsf(vol_pw(p, A - (m0 * i + m1 * j + mk)) - sk[q * STRIDE]);
+            e += fabsf(vol_pw_clamped(p, A - (m0 * i + m1 * j + mk)) - sk[q * STRIDE]);
         }
     }
     return {e * (1.f / 27.f), A - off};
