@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--train-samples", type=int, default=10_000_000)
     p.add_argument("--train-epochs", type=int, default=4)
     p.add_argument("--fp64-steps", type=int, default=3, help="steps of the FP64 comparison run")
-    p.add_argument("--e2e-steps", type=int, default=8)
+    p.add_argument("--e2e-steps", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=64, help="sub-box edge of the reference arm's sample")
