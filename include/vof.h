@@ -92,11 +92,8 @@ size_t vof_workspace_size(const vof_config *cfg);
  * lifetime (c is updated in place by vof_step / vof_recolour, u is read
  * only); workspace_dev must hold vof_workspace_size(cfg) bytes and be
  * 256-byte aligned.  Scans u once (synchronising `stream`): VOF_ERR_NONFINITE
- * if it holds NaN/Inf.  Fields k >= k_active must be zero.  Creates four
- * non-blocking streams and their events on the current device (released by
- * vof_destroy; VOF_ERR_CUDA if that fails): Step 2 tags the flagged fields
- * side by side on them, forked from and joined back to `stream` by events,
- * so every call stays ordered on `stream`.
+ * if it holds NaN/Inf.  Fields k >= k_active must be zero.  All of a
+ * context's work is enqueued on `stream` (no other stream is created).
  */
 vof_status vof_init(const vof_config *cfg, void *c_dev, const void *u_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream,
