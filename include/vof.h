@@ -127,7 +127,8 @@ typedef struct {
  * current field, face fluxes of the upwind donor's sub-cell, the
  * Weymouth-Yue term c_c (u_hi - u_lo) with c_c = [c > 1/2] of the step's
  * start, and a clip to [0,1] after the third sweep.  With cfg.recolour,
- * Steps 1-4 run after every step (synchronising once per step).
+ * Steps 1-4 run after every step (the host waits for Step 1's flags and,
+ * where drops are in near contact, for their tag pairs and touch tests).
  * VOF_ERR_CFL if max |u| dt / h > 1/2.  `report` may be NULL.  Asynchronous
  * when recolouring is off and report is NULL.
  */
